@@ -1,0 +1,20 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle.
+
+This package generates matrices only: it holds none of the Ozaki-II
+arithmetic and none of the LU.  Every generator is deterministic given its
+arguments (numpy default_rng seeds).
+
+  random_expansions   the standalone-GEMM workload (Sec. 4.2 style data):
+                      leading components uniform [-1, 1) times 2^e,
+                      e uniform in [emin, emax], each lower component random
+                      below a quarter ulp of the one before it
+  lotkin_expansions   the Lotkin matrix of Sec. 4.4 rounded component by
+                      component from exact rationals
+  lotkin_rhs          b = A * ones formed exactly from the rational matrix,
+                      then rounded
+"""
+from .matrices import (lotkin_expansions, lotkin_rhs, random_expansions,
+                       rational_to_expansion)
+
+__all__ = ["random_expansions", "lotkin_expansions", "lotkin_rhs",
+           "rational_to_expansion"]
