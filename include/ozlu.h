@@ -1,0 +1,152 @@
+/*
+ * ozlu.h -- C ABI of the GB300 Ozaki-scheme-II multiple-precision GEMM and LU.
+ *
+ * The operations follow T. Kouya, "Accelerating Multiple-Precision LU
+ * Decomposition with Ozaki Scheme II":
+ *   ozlu_gemm   the Ozaki-II GEMM, steps (S1)-(S6) of Sec. 3.1, with the
+ *               slice splitting and per-digit-group CRT of Sec. 3.2 (Eqs. (2),
+ *               (3), (8), (11)) and the direct expansion conversion of
+ *               Sec. 3.3 (Eq. (12));
+ *   ozlu_getrf  the blocked right-looking LU with partial pivoting of
+ *               Sec. 3.4, (P1)-(P4), whose trailing update Eq. (13),
+ *               A22 <- A22 - L21 U12, is an ozlu_gemm;
+ *   ozlu_getrs  the forward and backward substitution used in Sec. 4.4.
+ *
+ * Number format.  A multiple-precision element is a non-overlapping
+ * expansion of nc = 2, 3 or 4 binary64 components (DD, TD, QD; Sec. 2.1),
+ * stored as nc contiguous doubles, largest first.  Matrices are column-major:
+ * element (i, j) of a matrix with leading dimension ld starts at
+ * base + (i + j * ld) * nc doubles.  p is the target precision in bits
+ * (0 means 53 * nc).
+ *
+ * Memory.  Matrix, pivot and info pointers may be device pointers or host
+ * pointers (pageable or pinned).  Host arguments are copied to a device
+ * workspace and back inside the call, on the handle's stream, and the call
+ * then waits for the stream; device arguments are used in place and the call
+ * returns without waiting (stream ordered).  The caller owns every argument
+ * buffer.  The handle owns its workspace (residue planes, CRT inputs, plan
+ * tables), grown on demand and released by ozlu_destroy.
+ *
+ * Errors.  0 on success.  -i: argument i (1-based, handle = 1) is invalid.
+ * Positive: one of the OZLU_ERR_* codes.  A handle is not thread safe; use one
+ * handle per host thread.
+ */
+#ifndef OZLU_H
+#define OZLU_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ozlu_handle ozlu_handle;
+
+enum {
+    OZLU_OK = 0,
+    OZLU_ERR_CUDA = 1001,      /* a CUDA runtime call failed                     */
+    OZLU_ERR_NOMEM = 1002,     /* device workspace could not be allocated        */
+    OZLU_ERR_CAPACITY = 1003,  /* p, K or the format is beyond what a plan holds */
+    OZLU_ERR_TIMEOUT = 1004,   /* a bounded device wait gave up                  */
+    OZLU_ERR_UNSUPPORTED = 1005 /* back-end not available in this build/device   */
+};
+
+/* Residue back-ends of (S4) (Sec. 3.5, Table backend_origin). */
+enum {
+    OZLU_BE_AUTO = 0, /* measured choice per shape (autotuner)                        */
+    OZLU_BE_INT8 = 1, /* centered residues in int8, exact int32 accumulation          */
+    OZLU_BE_FP8 = 2,  /* balanced base-17 digits in E4M3, Eq. (15), fp32 accumulation */
+    OZLU_BE_FP64 = 3  /* residues of ~23-bit primes in binary64, Eq. (17)             */
+};
+
+/* Options; an all-zero struct (or NULL) selects the defaults. */
+typedef struct {
+    int backend;      /* OZLU_BE_*                                                 */
+    int nslice;       /* S override (Sec. 3.2); 0 = smallest feasible S            */
+    int extra_groups; /* digit groups kept below S-1 (Sec. 3.2, cancellation)      */
+    int g_ex;         /* extra guard bits in the slack of Sec. 3.2                 */
+    int reserved[12];
+} ozlu_opts;
+
+/* Plan of one Ozaki-II GEMM (Sec. 3.2 "Determining w and N"). */
+typedef struct {
+    int p, K, backend, S, w, Q, n_mod, g0, n_groups, pair_terms;
+    int moduli[64];   /* m_1 > m_2 > ... (descending), n_mod entries */
+} ozlu_plan_info;
+
+/* Create a handle bound to a CUDA stream (cudaStream_t passed as void*; NULL =
+ * the default stream).  The current device at creation is the handle's
+ * device.  Returns OZLU_ERR_CUDA when no device is usable. */
+int ozlu_create(ozlu_handle** handle, void* stream);
+/* Release the workspace and the handle.  NULL is accepted. */
+int ozlu_destroy(ozlu_handle* handle);
+int ozlu_set_stream(ozlu_handle* handle, void* stream);
+
+/* The plan ozlu_gemm uses for precision p, inner dimension k and options. */
+int ozlu_plan(int p, int k, const ozlu_opts* opts, ozlu_plan_info* out);
+
+/*
+ * C = beta * C + alpha * A * B  (Sec. 3.1, (S1)-(S6)).
+ *   nc      2, 3 or 4;  p in [1, 53*nc] (0 = 53*nc)
+ *   m, n, k >= 0 (k = 0 or m = 0 or n = 0: C is scaled by beta only)
+ *   alpha   +1 or -1;  beta 0 or 1
+ *   A       m x k expansions, lda >= max(1, m)
+ *   B       k x n expansions, ldb >= max(1, k)
+ *   C       m x n expansions, ldc >= max(1, m); not aliased with A or B
+ * Result: one rounding per element (S6): the exact integer of the retained
+ * digit groups, scaled by 2^-(mu_i + nu_j), plus beta * C brought to the same
+ * grid, rounded component by component to nc doubles.
+ */
+int ozlu_gemm(ozlu_handle* handle, int nc, int p, int m, int n, int k, int alpha,
+              const double* A, long long lda, const double* B, long long ldb,
+              int beta, double* C, long long ldc, const ozlu_opts* opts);
+
+/*
+ * Blocked LU with partial pivoting, P A = L U (Sec. 3.4, (P1)-(P4)).
+ *   A      n x n expansions, overwritten by L (unit, strictly below) and U
+ *   ipiv   n ints: row i was interchanged with row ipiv[i] (1-based, LAPACK)
+ *   nb     panel width b (0 = 256)
+ *   info   one int: 0, or the 1-based column of the first exactly zero pivot
+ *          (the factorisation continues, as in LAPACK)
+ * Panels (P1)-(P3) run in error-free expansion arithmetic; the trailing
+ * update (P4) is ozlu_gemm with alpha = -1, beta = 1.
+ */
+int ozlu_getrf(ozlu_handle* handle, int nc, int p, int n, double* A, long long lda,
+               int* ipiv, int nb, int* info, const ozlu_opts* opts);
+
+/*
+ * Solve A X = B from ozlu_getrf's factors (P b, forward L, backward U).
+ *   LU, ipiv  as returned by ozlu_getrf;  B n x nrhs, overwritten by X.
+ */
+int ozlu_getrs(ozlu_handle* handle, int nc, int p, int n, int nrhs,
+               const double* LU, long long lda, const int* ipiv,
+               double* B, long long ldb, const ozlu_opts* opts);
+
+/*
+ * Intermediates of the last ozlu_gemm on this handle, copied to host memory
+ * for parity checks against a reference (the workspace keeps them until the
+ * next call).  what:
+ *   1 mu  (m int32)        2 nu (n int32)
+ *   3 residues of A  int8 [l][t][i][h], h < k, planes (l, t) in order
+ *   4 residues of B  int8 [l][t][j][h]
+ *   5 t values      uint8 [gi][l][j][i] (column-major m x n per plane)
+ * bytes must be at least the size of the requested array.
+ */
+int ozlu_debug_fetch(ozlu_handle* handle, int what, void* dst, size_t bytes);
+
+/* Per-phase device times (ms) of the last ozlu_gemm / ozlu_getrf when
+ * timing is enabled with ozlu_set_timing(handle, 1). */
+typedef struct {
+    double convert_ms, gemm_ms, crt_ms, panel_ms, other_ms;
+    long long gemm_launches, crt_launches, panel_launches;
+} ozlu_stats;
+int ozlu_set_timing(ozlu_handle* handle, int enable);
+int ozlu_get_stats(ozlu_handle* handle, ozlu_stats* out);
+
+/* Version string of the library. */
+const char* ozlu_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* OZLU_H */

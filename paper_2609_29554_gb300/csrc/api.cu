@@ -1,0 +1,278 @@
+// C ABI entry points, handle and device workspace.
+#include <string.h>
+
+#include <map>
+#include <tuple>
+
+#include "ozlu_internal.h"
+#include "ozlu_handle.h"
+
+namespace ozlu {
+
+int cuda_rc(cudaError_t e) { return e == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA; }
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+int Workspace::ensure(size_t bytes) {
+    if (bytes <= cap) return OZLU_OK;
+    if (base) cudaFree(base);
+    base = nullptr;
+    cap = 0;
+    size_t want = bytes + bytes / 8;
+    if (cudaMalloc(&base, want) != cudaSuccess) {
+        cudaGetLastError();
+        if (cudaMalloc(&base, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            base = nullptr;
+            return OZLU_ERR_NOMEM;
+        }
+        want = bytes;
+    }
+    cap = want;
+    return OZLU_OK;
+}
+
+void Workspace::release() {
+    if (base) cudaFree(base);
+    base = nullptr;
+    cap = 0;
+}
+
+int plan_for(ozlu_handle* h, int p, int K, const ozlu_opts* o, const Plan** out,
+             const DevTable** tab) {
+    ozlu_opts d;
+    memset(&d, 0, sizeof d);
+    if (!o) o = &d;
+    auto key = std::make_tuple(p, K, o->backend, o->nslice, o->extra_groups, o->g_ex);
+    auto it = h->plans.find(key);
+    if (it == h->plans.end()) {
+        PlanEntry e;
+        int rc = make_plan(p, K, o, e.plan);
+        if (rc) return rc;
+        fill_table(e.plan, e.table);
+        it = h->plans.emplace(key, e).first;
+    }
+    *out = &it->second.plan;
+    *tab = &it->second.table;
+    return OZLU_OK;
+}
+
+static size_t align_up(size_t v) { return (v + 255) / 256 * 256; }
+
+// The device part of one GEMM, all pointers on the device.
+int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, const double* A,
+                long long lda, const double* B, long long ldb, int beta, double* C,
+                long long ldc, const ozlu_opts* opts) {
+    cudaStream_t s = h->stream;
+    if (m == 0 || n == 0) return OZLU_OK;
+    if (k == 0) {
+        if (beta == 0) {
+            for (int j = 0; j < n; ++j)
+                if (cudaMemsetAsync(C + (long long)j * ldc * nc, 0, sizeof(double) * nc * m, s))
+                    return OZLU_ERR_CUDA;
+        }
+        return OZLU_OK;
+    }
+    const Plan* pl;
+    const DevTable* tab;
+    int rc = plan_for(h, p, k, opts, &pl, &tab);
+    if (rc) return rc;
+    if (pl->backend != OZLU_BE_INT8) return OZLU_ERR_UNSUPPORTED;
+    const int Mpad = (m + 127) / 128 * 128, Npad = (n + 127) / 128 * 128;
+    const int Kpad = pl->Kpad;
+    GemmLayout& L = h->last;
+    L.m = m; L.n = n; L.k = k; L.Mpad = Mpad; L.Npad = Npad; L.Kpad = Kpad;
+    L.N = pl->N; L.S = pl->S; L.G = pl->G;
+    size_t off = 0;
+    L.mu = off; off = align_up(off + sizeof(int) * m);
+    L.nu = off; off = align_up(off + sizeof(int) * n);
+    L.ra = off; off = align_up(off + (size_t)pl->N * pl->S * Mpad * Kpad);
+    L.rb = off; off = align_up(off + (size_t)pl->N * pl->S * Npad * Kpad);
+    L.t = off;  off = align_up(off + (size_t)pl->G * pl->N * m * n);
+    rc = h->ws.ensure(off);
+    if (rc) return rc;
+    char* base = (char*)h->ws.base;
+    int* mu = (int*)(base + L.mu);
+    int* nu = (int*)(base + L.nu);
+    int8_t* RA = (int8_t*)(base + L.ra);
+    int8_t* RB = (int8_t*)(base + L.rb);
+    uint8_t* T = (uint8_t*)(base + L.t);
+    h->tic(0);
+    launch_row_shifts(A, lda, nc, m, k, pl->Q, mu, s);
+    launch_col_shifts(B, ldb, nc, k, n, pl->Q, nu, s);
+    launch_convert(A, lda, nc, m, k, false, mu, *tab, Kpad, Mpad, RA, s);
+    launch_convert(B, ldb, nc, k, n, true, nu, *tab, Kpad, Npad, RB, s);
+    h->tic(1);
+    launch_gemm_imma(RA, RB, m, n, Mpad, Npad, Kpad, *tab, T, s);
+    h->tic(2);
+    launch_crt(T, m, n, mu, nu, *tab, nc, alpha, beta, C, ldc, s);
+    h->tic(3);
+    h->stats.gemm_launches += 1;
+    h->stats.crt_launches += 1;
+    if (cudaGetLastError() != cudaSuccess) return OZLU_ERR_CUDA;
+    h->accumulate_times();
+    return OZLU_OK;
+}
+
+}  // namespace ozlu
+
+void ozlu_handle::tic(int idx) {
+    if (timing) cudaEventRecord(ev[idx], stream);
+}
+
+void ozlu_handle::accumulate_times() {
+    if (!timing) return;
+    cudaEventSynchronize(ev[3]);
+    float a = 0, b = 0, c = 0;
+    cudaEventElapsedTime(&a, ev[0], ev[1]);
+    cudaEventElapsedTime(&b, ev[1], ev[2]);
+    cudaEventElapsedTime(&c, ev[2], ev[3]);
+    stats.convert_ms += a;
+    stats.gemm_ms += b;
+    stats.crt_ms += c;
+}
+
+
+using namespace ozlu;
+
+extern "C" {
+
+const char* ozlu_version(void) { return "ozlu 0.1 (sm_103a)"; }
+
+int ozlu_create(ozlu_handle** handle, void* stream) {
+    if (!handle) return -1;
+    *handle = nullptr;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return OZLU_ERR_CUDA;
+    }
+    ozlu_handle* h = new ozlu_handle();
+    h->device = dev;
+    h->stream = (cudaStream_t)stream;
+    for (auto& e : h->ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            delete h;
+            return OZLU_ERR_CUDA;
+        }
+    *handle = h;
+    return OZLU_OK;
+}
+
+int ozlu_destroy(ozlu_handle* h) {
+    if (!h) return OZLU_OK;
+    cudaStreamSynchronize(h->stream);
+    h->ws.release();
+    h->stage.release();
+    for (auto& e : h->ev) cudaEventDestroy(e);
+    delete h;
+    return OZLU_OK;
+}
+
+int ozlu_set_stream(ozlu_handle* h, void* stream) {
+    if (!h) return -1;
+    h->stream = (cudaStream_t)stream;
+    return OZLU_OK;
+}
+
+int ozlu_set_timing(ozlu_handle* h, int enable) {
+    if (!h) return -1;
+    h->timing = enable != 0;
+    memset(&h->stats, 0, sizeof h->stats);
+    return OZLU_OK;
+}
+
+int ozlu_get_stats(ozlu_handle* h, ozlu_stats* out) {
+    if (!h) return -1;
+    if (!out) return -2;
+    *out = h->stats;
+    return OZLU_OK;
+}
+
+int ozlu_gemm(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, const double* A,
+              long long lda, const double* B, long long ldb, int beta, double* C, long long ldc,
+              const ozlu_opts* opts) {
+    if (!h) return -1;
+    if (nc < 2 || nc > 4) return -2;
+    if (p == 0) p = 53 * nc;
+    if (p < 1 || p > 53 * nc) return -3;
+    if (m < 0) return -4;
+    if (n < 0) return -5;
+    if (k < 0) return -6;
+    if (alpha != 1 && alpha != -1) return -7;
+    if (!A && m && k) return -8;
+    if (lda < (m > 1 ? m : 1)) return -9;
+    if (!B && k && n) return -10;
+    if (ldb < (k > 1 ? k : 1)) return -11;
+    if (beta != 0 && beta != 1) return -12;
+    if (!C && m && n) return -13;
+    if (ldc < (m > 1 ? m : 1)) return -14;
+    if (cudaSetDevice(h->device) != cudaSuccess) return OZLU_ERR_CUDA;
+    const bool dA = !A || is_device_ptr(A), dB = !B || is_device_ptr(B), dC = !C || is_device_ptr(C);
+    if (dA && dB && dC) return gemm_device(h, nc, p, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, opts);
+    // stage host operands through a second device buffer
+    const size_t ea = (size_t)lda * (k ? k : 1) * nc, eb = (size_t)ldb * (n ? n : 1) * nc,
+                 ec = (size_t)ldc * (n ? n : 1) * nc;
+    const size_t bytes = sizeof(double) * (ea + eb + ec) + 3 * 256;
+    int rc = h->stage.ensure(bytes);
+    if (rc) return rc;
+    double* sA = (double*)h->stage.base;
+    double* sB = (double*)((char*)sA + align_up(sizeof(double) * ea));
+    double* sC = (double*)((char*)sB + align_up(sizeof(double) * eb));
+    cudaStream_t s = h->stream;
+    const double* gA = A;
+    const double* gB = B;
+    double* gC = C;
+    if (!dA) { if (cudaMemcpyAsync(sA, A, sizeof(double) * ea, cudaMemcpyHostToDevice, s)) return OZLU_ERR_CUDA; gA = sA; }
+    if (!dB) { if (cudaMemcpyAsync(sB, B, sizeof(double) * eb, cudaMemcpyHostToDevice, s)) return OZLU_ERR_CUDA; gB = sB; }
+    if (!dC) {
+        if (beta && cudaMemcpyAsync(sC, C, sizeof(double) * ec, cudaMemcpyHostToDevice, s)) return OZLU_ERR_CUDA;
+        gC = sC;
+    }
+    rc = gemm_device(h, nc, p, m, n, k, alpha, gA, lda, gB, ldb, beta, gC, ldc, opts);
+    if (rc) return rc;
+    if (!dC && cudaMemcpyAsync(C, sC, sizeof(double) * ec, cudaMemcpyDeviceToHost, s)) return OZLU_ERR_CUDA;
+    return cuda_rc(cudaStreamSynchronize(s));
+}
+
+int ozlu_debug_fetch(ozlu_handle* h, int what, void* dst, size_t bytes) {
+    if (!h) return -1;
+    if (!dst) return -3;
+    const GemmLayout& L = h->last;
+    char* base = (char*)h->ws.base;
+    if (!base) return OZLU_ERR_CAPACITY;
+    if (cudaStreamSynchronize(h->stream)) return OZLU_ERR_CUDA;
+    if (what == 1 || what == 2) {
+        const size_t need = sizeof(int) * (what == 1 ? L.m : L.n);
+        if (bytes < need) return -4;
+        return cuda_rc(cudaMemcpy(dst, base + (what == 1 ? L.mu : L.nu), need, cudaMemcpyDeviceToHost));
+    }
+    if (what == 3 || what == 4) {
+        const int R = what == 3 ? L.m : L.n, Rpad = what == 3 ? L.Mpad : L.Npad;
+        const size_t need = (size_t)L.N * L.S * R * L.k;
+        if (bytes < need) return -4;
+        const char* src = base + (what == 3 ? L.ra : L.rb);
+        for (int pl = 0; pl < L.N * L.S; ++pl)
+            if (cudaMemcpy2D((char*)dst + (size_t)pl * R * L.k, L.k, src + (size_t)pl * Rpad * L.Kpad,
+                             L.Kpad, L.k, R, cudaMemcpyDeviceToHost) != cudaSuccess)
+                return OZLU_ERR_CUDA;
+        return OZLU_OK;
+    }
+    if (what == 5) {
+        const size_t need = (size_t)L.G * L.N * L.m * L.n;
+        if (bytes < need) return -4;
+        return cuda_rc(cudaMemcpy(dst, base + L.t, need, cudaMemcpyDeviceToHost));
+    }
+    return -2;
+}
+
+}  // extern "C"

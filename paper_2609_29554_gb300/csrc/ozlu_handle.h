@@ -1,0 +1,51 @@
+// The handle: stream, device workspace, plan cache, last-GEMM layout, timers.
+#pragma once
+
+#include <map>
+#include <tuple>
+
+#include "ozlu_internal.h"
+
+namespace ozlu {
+
+struct Workspace {
+    void* base = nullptr;
+    size_t cap = 0;
+    int ensure(size_t bytes);
+    void release();
+};
+
+struct PlanEntry {
+    Plan plan;
+    DevTable table;
+};
+
+// byte offsets of the last ozlu_gemm's intermediates inside the workspace
+struct GemmLayout {
+    int m = 0, n = 0, k = 0, Mpad = 0, Npad = 0, Kpad = 0, N = 0, S = 0, G = 0;
+    size_t mu = 0, nu = 0, ra = 0, rb = 0, t = 0;
+};
+
+}  // namespace ozlu
+
+struct ozlu_handle {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    ozlu::Workspace ws;     // GEMM intermediates
+    ozlu::Workspace stage;  // host-argument staging
+    std::map<std::tuple<int, int, int, int, int, int>, ozlu::PlanEntry> plans;
+    ozlu::GemmLayout last;
+    bool timing = false;
+    ozlu_stats stats = {};
+    cudaEvent_t ev[4] = {};
+    void tic(int idx);
+    void accumulate_times();
+};
+
+namespace ozlu {
+int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, const double* A,
+                long long lda, const double* B, long long ldb, int beta, double* C,
+                long long ldc, const ozlu_opts* opts);
+bool is_device_ptr(const void* p);
+int cuda_rc(cudaError_t e);
+}  // namespace ozlu

@@ -1,0 +1,69 @@
+// Internal declarations shared by the ozlu host code and kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/ozlu.h"
+
+namespace ozlu {
+
+constexpr int MAXMOD = 64;       // moduli per plan (INT8 set has 54)
+constexpr int MAXH = 16;         // 16-bit halves of one balanced digit (w < 256)
+constexpr int MAXWG = 12;        // 32-bit words of one digit-group integer S_g
+constexpr int WACC = 16;         // 32-bit words of the fused output window
+constexpr int WINDOW_BITS = 510; // window width above the grid 2^E (sign bit spare)
+constexpr int MAXWX = 12;        // 32-bit words of one Q-bit fixed-point input
+constexpr int MAXG = 8;          // retained digit groups
+
+// Host-side plan (Sec. 3.2 "Determining w and N").
+struct Plan {
+    int p = 0, K = 0, Kpad = 0, backend = OZLU_BE_INT8, g_ex = 0, extra = 0;
+    int S = 0, w = 0, Q = 0, N = 0, g0 = 0, G = 0, pair_terms = 0;
+    double need = 0.0;
+    int mod[MAXMOD] = {0};
+    int y[MAXMOD] = {0};
+    std::vector<uint32_t> P;               // P = prod m_l, little-endian words
+    std::vector<std::vector<uint32_t>> M;  // M_l = P / m_l
+    int sbar_bits = 0, WG = 0, pint_bits = 0, WX = 0, H = 0;
+};
+
+// Constant table of one plan, passed to kernels by value (__grid_constant__).
+struct DevTable {
+    int N, WG, H, S, w, g0, G, Q, WX;
+    int mod[MAXMOD];
+    int y[MAXMOD];
+    uint32_t magic[MAXMOD];   // ceil(2^32 / m): x mod m by one __umulhi
+    float invm[MAXMOD];       // 1/m for F = sum t_l / m_l (Eq. (11))
+    uint32_t pow16[MAXMOD][MAXH];  // 2^(16 j) mod m
+    uint32_t Mlow[MAXMOD][MAXWG];  // M_l mod 2^(32 WG)
+    uint32_t Plow[MAXWG];          // P mod 2^(32 WG)
+};
+
+int make_plan(int p, int K, const ozlu_opts* o, Plan& out);
+void fill_table(const Plan& pl, DevTable& t);
+
+// ---------------------------------------------------------------- kernels --
+// (S1) shared exponents: mu[i] over rows of A (m x k), nu[j] over columns of B.
+void launch_row_shifts(const double* A, long long lda, int nc, int m, int k, int Q,
+                       int* mu, cudaStream_t s);
+void launch_col_shifts(const double* B, long long ldb, int nc, int k, int n, int Q,
+                       int* nu, cudaStream_t s);
+// (S2)+(S3) fused: expansions -> Q-bit integers -> S digits -> residue planes.
+// A side: planes [l][t][Mpad][Kpad] (row i, K contiguous); B side: [l][t][Npad][Kpad].
+void launch_convert(const double* X, long long ld, int nc, int rows, int cols,
+                    bool is_b, const int* shifts, const DevTable& tab, int Kpad,
+                    int Rpad, int8_t* planes, cudaStream_t s);
+// (S4)+(S5 t_l) INT8 residue GEMMs with the modular epilogue; T[gi][l][j][i].
+void launch_gemm_imma(const int8_t* RA, const int8_t* RB, int m, int n, int Mpad,
+                      int Npad, int Kpad, const DevTable& tab, uint8_t* T,
+                      cudaStream_t s);
+// (S5)+(S6): CRT per digit group, recombination, fused beta*C + alpha*AB, rounding.
+void launch_crt(const uint8_t* T, int m, int n, const int* mu, const int* nu,
+                const DevTable& tab, int nc, int alpha, int beta, double* C,
+                long long ldc, cudaStream_t s);
+
+}  // namespace ozlu

@@ -1,0 +1,184 @@
+// Host planner: modulus set, CRT constants and the (S, w, N_mod) rule.
+//
+// Sec. 3.2: the 54 pairwise-coprime maximal prime powers <= 255 (taken in
+// descending order), slack = ceil(log2 2K) + 16 + g_ex, and for S = 1, 2, ...
+// w = ceil((p + slack)/S), need = 2w + log2 K + log2 S + 5, N_mod = the
+// number of moduli whose cumulative log2 first exceeds need; the smallest S
+// that has such an N_mod and meets the accumulator condition is taken.
+// CRT constants M_l = P/m_l and y_l = M_l^-1 mod m_l (Eq. (11)).
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "ozlu_internal.h"
+
+namespace ozlu {
+namespace {
+
+bool is_prime(int v) {
+    if (v < 2) return false;
+    for (int d = 2; (long long)d * d <= v; ++d)
+        if (v % d == 0) return false;
+    return true;
+}
+
+std::vector<int> int8_set() {
+    std::vector<int> ms;
+    for (int q = 2; q <= 255; ++q) {
+        if (!is_prime(q)) continue;
+        int v = q;
+        while (v * q <= 255) v *= q;
+        ms.push_back(v);
+    }
+    std::sort(ms.begin(), ms.end(), [](int a, int b) { return a > b; });
+    return ms;
+}
+
+// Eq. (17): K (m/2)^2 < 2^53, largest primes first.
+std::vector<int> fp64_set(int K, int count) {
+    const unsigned __int128 lim = (unsigned __int128)1 << 55;
+    long long b = (long long)floor(sqrt(ldexp(1.0, 55) / K));
+    while (b > 1 && (unsigned __int128)K * b * b >= lim) --b;
+    while ((unsigned __int128)K * (b + 1) * (b + 1) < lim) ++b;
+    std::vector<int> ms;
+    for (long long v = b; v > 2 && (int)ms.size() < count; --v)
+        if (is_prime((int)v)) ms.push_back((int)v);
+    return ms;
+}
+
+void mul_small(std::vector<uint32_t>& a, uint32_t f) {
+    uint64_t carry = 0;
+    for (auto& w : a) {
+        uint64_t v = (uint64_t)w * f + carry;
+        w = (uint32_t)v;
+        carry = v >> 32;
+    }
+    if (carry) a.push_back((uint32_t)carry);
+}
+
+std::vector<uint32_t> div_small(const std::vector<uint32_t>& a, uint32_t d) {
+    std::vector<uint32_t> q(a.size());
+    uint64_t rem = 0;
+    for (int i = (int)a.size() - 1; i >= 0; --i) {
+        uint64_t cur = (rem << 32) | a[i];
+        q[i] = (uint32_t)(cur / d);
+        rem = cur % d;
+    }
+    while (q.size() > 1 && q.back() == 0) q.pop_back();
+    return q;
+}
+
+uint32_t mod_small(const std::vector<uint32_t>& a, uint32_t d) {
+    uint64_t rem = 0;
+    for (int i = (int)a.size() - 1; i >= 0; --i) rem = ((rem << 32) | a[i]) % d;
+    return (uint32_t)rem;
+}
+
+int inv_mod(int a, int m) {
+    long long t = 0, nt = 1, r = m, nr = a % m;
+    while (nr) {
+        long long q = r / nr;
+        long long tmp = t - q * nt; t = nt; nt = tmp;
+        tmp = r - q * nr; r = nr; nr = tmp;
+    }
+    if (t < 0) t += m;
+    return (int)t;
+}
+
+int ceil_log2(double v) { return (int)ceil(log2(v) - 1e-12); }
+
+}  // namespace
+
+int make_plan(int p, int K, const ozlu_opts* o, Plan& out) {
+    ozlu_opts d;
+    memset(&d, 0, sizeof d);
+    if (!o) o = &d;
+    const int be = o->backend == OZLU_BE_AUTO ? OZLU_BE_INT8 : o->backend;
+    if (p < 1 || K < 1) return OZLU_ERR_CAPACITY;
+    if (be != OZLU_BE_INT8 && be != OZLU_BE_FP8 && be != OZLU_BE_FP64) return -1;
+    const int slack = ceil_log2(2.0 * K) + 16 + o->g_ex;
+    const int Kpad = (K + 127) / 128 * 128;
+    std::vector<int> mods = be == OZLU_BE_FP64 ? fp64_set(K, MAXMOD) : int8_set();
+    int s_lo = o->nslice > 0 ? o->nslice : 1;
+    int s_hi = o->nslice > 0 ? o->nslice : 64;
+    for (int S = s_lo; S <= s_hi; ++S) {
+        // accumulator conditions: INT32 (Sec. 3.2), FP32 for the base-17
+        // Karatsuba planes (|digit sums| <= 15)
+        if (be == OZLU_BE_INT8 && (double)Kpad * S * 127.0 * 127.0 >= ldexp(1.0, 31)) continue;
+        if (be == OZLU_BE_FP8 && (double)Kpad * S * 225.0 >= ldexp(1.0, 24)) continue;
+        const int w = (p + slack + S - 1) / S;
+        const double need = 2.0 * w + log2((double)K) + log2((double)S) + 5.0;
+        double cum = 0.0;
+        int N = 0;
+        for (int i = 0; i < (int)mods.size(); ++i) {
+            cum += log2((double)mods[i]);
+            if (cum > need) { N = i + 1; break; }
+        }
+        if (N == 0) continue;
+        Plan pl;
+        pl.p = p; pl.K = K; pl.Kpad = Kpad; pl.backend = be; pl.g_ex = o->g_ex;
+        pl.extra = o->extra_groups < 0 ? 0 : o->extra_groups;
+        pl.S = S; pl.w = w; pl.Q = w * S; pl.N = N; pl.need = need;
+        pl.g0 = std::max(0, S - 1 - pl.extra);
+        pl.G = 2 * S - 1 - pl.g0;
+        pl.pair_terms = 0;
+        for (int g = pl.g0; g <= 2 * S - 2; ++g) pl.pair_terms += std::min(g, 2 * S - 2 - g) + 1;
+        std::vector<uint32_t> P{1};
+        for (int i = 0; i < N; ++i) { pl.mod[i] = mods[i]; mul_small(P, (uint32_t)mods[i]); }
+        pl.P = P;
+        pl.M.resize(N);
+        for (int i = 0; i < N; ++i) {
+            pl.M[i] = div_small(P, (uint32_t)mods[i]);
+            pl.y[i] = inv_mod((int)mod_small(pl.M[i], (uint32_t)mods[i]), mods[i]);
+        }
+        // |S_g| <= pairs K 2^(2w-2), pairs <= S: two's complement width
+        pl.sbar_bits = 2 * w - 1 + ceil_log2((double)S * K) + 1;
+        pl.WG = (pl.sbar_bits + 31) / 32;
+        pl.pint_bits = w * (2 * S - 2 - pl.g0) + pl.sbar_bits;
+        pl.WX = (pl.Q + 1 + 31) / 32;
+        pl.H = (w + 1 + 15) / 16;
+        if (N > MAXMOD || pl.WG > MAXWG || pl.WX > MAXWX || pl.H > MAXH || pl.G > MAXG ||
+            pl.pint_bits + 2 > WINDOW_BITS)
+            return OZLU_ERR_CAPACITY;
+        out = pl;
+        return OZLU_OK;
+    }
+    return OZLU_ERR_CAPACITY;
+}
+
+void fill_table(const Plan& pl, DevTable& t) {
+    memset(&t, 0, sizeof t);
+    t.N = pl.N; t.WG = pl.WG; t.H = pl.H; t.S = pl.S; t.w = pl.w; t.g0 = pl.g0;
+    t.G = pl.G; t.Q = pl.Q; t.WX = pl.WX;
+    for (int l = 0; l < pl.N; ++l) {
+        const uint32_t m = (uint32_t)pl.mod[l];
+        t.mod[l] = (int)m;
+        t.y[l] = pl.y[l];
+        t.magic[l] = (uint32_t)(((1ull << 32) + m - 1) / m);
+        t.invm[l] = 1.0f / (float)m;
+        uint64_t r = 1 % m;
+        for (int j = 0; j < MAXH; ++j) {
+            t.pow16[l][j] = (uint32_t)r;
+            r = (r << 16) % m;
+        }
+        for (int wd = 0; wd < pl.WG; ++wd)
+            t.Mlow[l][wd] = wd < (int)pl.M[l].size() ? pl.M[l][wd] : 0u;
+    }
+    for (int wd = 0; wd < pl.WG; ++wd) t.Plow[wd] = wd < (int)pl.P.size() ? pl.P[wd] : 0u;
+}
+
+}  // namespace ozlu
+
+extern "C" int ozlu_plan(int p, int k, const ozlu_opts* opts, ozlu_plan_info* out) {
+    if (!out) return -4;
+    ozlu::Plan pl;
+    int rc = ozlu::make_plan(p, k, opts, pl);
+    if (rc) return rc;
+    memset(out, 0, sizeof *out);
+    out->p = pl.p; out->K = pl.K; out->backend = pl.backend; out->S = pl.S; out->w = pl.w;
+    out->Q = pl.Q; out->n_mod = pl.N; out->g0 = pl.g0; out->n_groups = pl.G;
+    out->pair_terms = pl.pair_terms;
+    for (int i = 0; i < pl.N && i < 64; ++i) out->moduli[i] = pl.mod[i];
+    return OZLU_OK;
+}

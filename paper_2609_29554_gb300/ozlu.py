@@ -1,0 +1,184 @@
+"""Python binding of the ozlu C ABI (include/ozlu.h): argument marshalling only.
+
+Every entry point of the shared library has a function of the same name here.
+Matrices are passed as torch tensors (device memory, used in place) or numpy
+arrays (host memory, staged by the library).  An expansion matrix with
+leading dimension ld and c columns is a float64 array of shape (c, ld, nc),
+contiguous: column-major storage with nc components per element.
+
+The library is required: importing a function that needs it raises
+RuntimeError when libozlu.so has not been built (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libozlu.so")
+
+OZLU_OK = 0
+OZLU_ERR_CUDA = 1001
+OZLU_ERR_NOMEM = 1002
+OZLU_ERR_CAPACITY = 1003
+OZLU_ERR_TIMEOUT = 1004
+OZLU_ERR_UNSUPPORTED = 1005
+BACKENDS = {"auto": 0, "int8": 1, "fp8": 2, "fp64": 3}
+
+_lib = None
+
+
+class ozlu_opts(ctypes.Structure):
+    _fields_ = [("backend", ctypes.c_int), ("nslice", ctypes.c_int),
+                ("extra_groups", ctypes.c_int), ("g_ex", ctypes.c_int),
+                ("reserved", ctypes.c_int * 12)]
+
+
+class ozlu_plan_info(ctypes.Structure):
+    _fields_ = [(f, ctypes.c_int) for f in ("p", "K", "backend", "S", "w", "Q", "n_mod",
+                                             "g0", "n_groups", "pair_terms")] + \
+               [("moduli", ctypes.c_int * 64)]
+
+
+class ozlu_stats(ctypes.Structure):
+    _fields_ = [("convert_ms", ctypes.c_double), ("gemm_ms", ctypes.c_double),
+                ("crt_ms", ctypes.c_double), ("panel_ms", ctypes.c_double),
+                ("other_ms", ctypes.c_double), ("gemm_launches", ctypes.c_longlong),
+                ("crt_launches", ctypes.c_longlong), ("panel_launches", ctypes.c_longlong)]
+
+
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_L = ctypes.c_longlong
+SIGNATURES = {
+    "ozlu_version": (ctypes.c_char_p, []),
+    "ozlu_create": (_I, [ctypes.POINTER(_P), _P]),
+    "ozlu_destroy": (_I, [_P]),
+    "ozlu_set_stream": (_I, [_P, _P]),
+    "ozlu_plan": (_I, [_I, _I, ctypes.POINTER(ozlu_opts), ctypes.POINTER(ozlu_plan_info)]),
+    "ozlu_gemm": (_I, [_P, _I, _I, _I, _I, _I, _I, _P, _L, _P, _L, _I, _P, _L,
+                       ctypes.POINTER(ozlu_opts)]),
+    "ozlu_getrf": (_I, [_P, _I, _I, _I, _P, _L, _P, _I, _P, ctypes.POINTER(ozlu_opts)]),
+    "ozlu_getrs": (_I, [_P, _I, _I, _I, _I, _P, _L, _P, _P, _L, ctypes.POINTER(ozlu_opts)]),
+    "ozlu_debug_fetch": (_I, [_P, _I, _P, ctypes.c_size_t]),
+    "ozlu_set_timing": (_I, [_P, _I]),
+    "ozlu_get_stats": (_I, [_P, ctypes.POINTER(ozlu_stats)]),
+}
+
+
+def lib():
+    """The loaded libozlu.so; raises RuntimeError when it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libozlu.so is not built: run paper_2609_29554_gb300.build.build()")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+class OzluError(RuntimeError):
+    def __init__(self, fn, code):
+        super().__init__(f"{fn} returned {code}")
+        self.code = code
+
+
+def _check(fn, code):
+    if code != OZLU_OK:
+        raise OzluError(fn, code)
+
+
+def make_opts(backend="int8", nslice=0, extra_groups=0, g_ex=0):
+    o = ozlu_opts()
+    o.backend = BACKENDS[backend] if isinstance(backend, str) else int(backend)
+    o.nslice, o.extra_groups, o.g_ex = nslice, extra_groups, g_ex
+    return o
+
+
+def _ptr(x):
+    """Device pointer of a torch tensor, host pointer of a numpy array."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        assert x.flags["C_CONTIGUOUS"]
+        return x.ctypes.data
+    return x.data_ptr()  # torch tensor
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        return None
+    return getattr(stream, "cuda_stream", stream)
+
+
+def ozlu_version():
+    return lib().ozlu_version().decode()
+
+
+def ozlu_create(stream=None):
+    h = _P()
+    _check("ozlu_create", lib().ozlu_create(ctypes.byref(h), _stream_ptr(stream)))
+    return h
+
+
+def ozlu_destroy(h):
+    _check("ozlu_destroy", lib().ozlu_destroy(h))
+
+
+def ozlu_set_stream(h, stream):
+    _check("ozlu_set_stream", lib().ozlu_set_stream(h, _stream_ptr(stream)))
+
+
+def ozlu_plan(p, k, opts=None):
+    info = ozlu_plan_info()
+    _check("ozlu_plan", lib().ozlu_plan(p, k, ctypes.byref(opts) if opts else None,
+                                        ctypes.byref(info)))
+    return info
+
+
+def ozlu_gemm(h, nc, p, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, opts=None):
+    _check("ozlu_gemm", lib().ozlu_gemm(h, nc, p, m, n, k, alpha, _ptr(A), lda, _ptr(B), ldb,
+                                        beta, _ptr(C), ldc,
+                                        ctypes.byref(opts) if opts else None))
+
+
+def ozlu_getrf(h, nc, p, n, A, lda, ipiv, nb, info, opts=None):
+    _check("ozlu_getrf", lib().ozlu_getrf(h, nc, p, n, _ptr(A), lda, _ptr(ipiv), nb, _ptr(info),
+                                          ctypes.byref(opts) if opts else None))
+
+
+def ozlu_getrs(h, nc, p, n, nrhs, LU, lda, ipiv, B, ldb, opts=None):
+    _check("ozlu_getrs", lib().ozlu_getrs(h, nc, p, n, nrhs, _ptr(LU), lda, _ptr(ipiv), _ptr(B),
+                                          ldb, ctypes.byref(opts) if opts else None))
+
+
+def ozlu_debug_fetch(h, what, out: np.ndarray):
+    _check("ozlu_debug_fetch", lib().ozlu_debug_fetch(h, what, out.ctypes.data, out.nbytes))
+    return out
+
+
+def ozlu_set_timing(h, enable):
+    _check("ozlu_set_timing", lib().ozlu_set_timing(h, int(enable)))
+
+
+def ozlu_get_stats(h):
+    st = ozlu_stats()
+    _check("ozlu_get_stats", lib().ozlu_get_stats(h, ctypes.byref(st)))
+    return st
+
+
+# ----------------------------------------------------------- layouts -----
+def to_colmajor(X: np.ndarray) -> np.ndarray:
+    """(rows, cols, nc) -> contiguous (cols, rows, nc): column-major, ld = rows."""
+    return np.ascontiguousarray(np.transpose(X, (1, 0, 2)))
+
+
+def from_colmajor(Y: np.ndarray, rows: int) -> np.ndarray:
+    """(cols, ld, nc) column-major -> (rows, cols, nc)."""
+    return np.ascontiguousarray(np.transpose(Y[:, :rows, :], (1, 0, 2)))

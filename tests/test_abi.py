@@ -1,0 +1,59 @@
+"""CPU checks of the C-ABI library: it builds, loads, exports every symbol
+include/ozlu.h declares, and its planner agrees with the oracle's plan."""
+import os
+import re
+
+import pytest
+
+from oracle.plan import make_plan
+from paper_2609_29554_gb300 import build, ozlu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return ozlu.lib()
+
+
+def declared_symbols():
+    text = open(os.path.join(ROOT, "include", "ozlu.h")).read()
+    return sorted(set(re.findall(r"\b(ozlu_[a-z_]+)\s*\(", text)))
+
+
+def test_exports_every_declared_symbol(L):
+    names = declared_symbols()
+    assert "ozlu_gemm" in names and "ozlu_getrf" in names and "ozlu_getrs" in names
+    for name in names:
+        assert hasattr(L, name), name
+        assert name in ozlu.SIGNATURES, name
+
+
+@pytest.mark.parametrize("p,k,be,S,extra,gex", [
+    (106, 512, "int8", 0, 0, 0), (159, 512, "int8", 0, 0, 0), (212, 512, "int8", 0, 0, 0),
+    (212, 256, "int8", 0, 0, 0), (106, 32, "int8", 0, 0, 0), (212, 4096, "int8", 0, 0, 0),
+    (159, 64, "int8", 0, 0, 0), (212, 100, "int8", 3, 0, 0), (212, 256, "int8", 0, 1, 0),
+    (212, 1024, "int8", 0, 0, 64), (212, 256, "fp8", 0, 0, 0), (106, 512, "fp64", 0, 0, 0),
+    (212, 512, "fp64", 2, 0, 0)])
+def test_plan_matches_oracle(L, p, k, be, S, extra, gex):
+    info = ozlu.ozlu_plan(p, k, ozlu.make_opts(be, S, extra, gex))
+    ref = make_plan(p, k, backend=be, S=S or None, extra_groups=extra, g_ex=gex)
+    assert (info.S, info.w, info.Q, info.n_mod, info.g0) == (ref.S, ref.w, ref.Q, ref.N, ref.g0)
+    assert list(info.moduli)[:info.n_mod] == list(ref.moduli)
+    assert info.pair_terms == ref.pair_terms
+
+
+def test_bad_arguments_rejected(L):
+    # argument checks happen before any device work
+    rc = L.ozlu_gemm(None, 4, 0, 1, 1, 1, 1, None, 1, None, 1, 0, None, 1, None)
+    assert rc == -1
+    with pytest.raises(ozlu.OzluError):
+        ozlu.ozlu_plan(0, 16)
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(ozlu, "LIB_PATH", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(ozlu, "_lib", None)
+    with pytest.raises(RuntimeError):
+        ozlu.lib()
