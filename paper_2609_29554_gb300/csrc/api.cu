@@ -173,6 +173,7 @@ int ozlu_destroy(ozlu_handle* h) {
     cudaStreamSynchronize(h->stream);
     h->ws.release();
     h->stage.release();
+    if (h->lu_scratch) cudaFree(h->lu_scratch);
     for (auto& e : h->ev) cudaEventDestroy(e);
     delete h;
     return OZLU_OK;

@@ -38,6 +38,7 @@ struct ozlu_handle {
     bool timing = false;
     ozlu_stats stats = {};
     cudaEvent_t ev[4] = {};
+    void* lu_scratch = nullptr;  // pivot-search scratch of ozlu_getrf
     void tic(int idx);
     void accumulate_times();
 };
