@@ -134,11 +134,20 @@ int ozlu_getrs(ozlu_handle* handle, int nc, int p, int n, int nrhs,
  */
 int ozlu_debug_fetch(ozlu_handle* handle, int what, void* dst, size_t bytes);
 
-/* Per-phase device times (ms) of the last ozlu_gemm / ozlu_getrf when
- * timing is enabled with ozlu_set_timing(handle, 1). */
+/* Counters since the last ozlu_set_timing call.  With timing enabled the
+ * library records CUDA events around each phase on the handle's stream
+ * (no host synchronisation until ozlu_get_stats resolves them):
+ *   convert_ms  (S1)-(S3) exponents, conversion and residues
+ *   gemm_ms     (S4) residue GEMMs with the modular epilogue
+ *   crt_ms      (S5)-(S6) CRT, recombination and rounding
+ *   panel_ms    (P1)-(P3) expansion-arithmetic kernels of the LU
+ * launches counts every kernel the library launched; gemm_ops, crt_bytes and
+ * convert_bytes are the algorithmic work of those phases (tensor operations
+ * 2 M N K per residue product, and the bytes each phase must move). */
 typedef struct {
     double convert_ms, gemm_ms, crt_ms, panel_ms, other_ms;
-    long long gemm_launches, crt_launches, panel_launches;
+    long long gemm_launches, crt_launches, panel_launches, launches;
+    double gemm_ops, crt_bytes, convert_bytes;
 } ozlu_stats;
 int ozlu_set_timing(ozlu_handle* handle, int enable);
 int ozlu_get_stats(ozlu_handle* handle, ozlu_stats* out);

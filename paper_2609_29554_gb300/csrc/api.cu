@@ -105,41 +105,67 @@ int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, c
     int8_t* RA = (int8_t*)(base + L.ra);
     int8_t* RB = (int8_t*)(base + L.rb);
     uint8_t* T = (uint8_t*)(base + L.t);
-    h->tic(0);
+    const int prev = h->open_phase;
+    h->phase(PH_CONVERT);
     launch_row_shifts(A, lda, nc, m, k, pl->Q, mu, s);
     launch_col_shifts(B, ldb, nc, k, n, pl->Q, nu, s);
     launch_convert(A, lda, nc, m, k, false, mu, *tab, Kpad, Mpad, RA, s);
     launch_convert(B, ldb, nc, k, n, true, nu, *tab, Kpad, Npad, RB, s);
-    h->tic(1);
+    h->phase(PH_GEMM);
     launch_gemm_imma(RA, RB, m, n, Mpad, Npad, Kpad, *tab, T, s);
-    h->tic(2);
+    h->phase(PH_CRT);
     launch_crt(T, m, n, mu, nu, *tab, nc, alpha, beta, C, ldc, s);
-    h->tic(3);
+    h->phase(prev);
     h->stats.gemm_launches += 1;
     h->stats.crt_launches += 1;
+    h->stats.gemm_ops += 2.0 * m * n * (double)k * pl->N * pl->pair_terms;
+    h->stats.crt_bytes += (double)pl->G * pl->N * m * n + 8.0 * nc * m * n * (beta ? 2 : 1);
+    h->stats.convert_bytes += 8.0 * nc * ((double)m * k + (double)k * n) +
+                              (double)pl->N * pl->S * ((double)Mpad + Npad) * Kpad;
+    h->count(6);
     if (cudaGetLastError() != cudaSuccess) return OZLU_ERR_CUDA;
-    h->accumulate_times();
     return OZLU_OK;
 }
 
 }  // namespace ozlu
 
-void ozlu_handle::tic(int idx) {
-    if (timing) cudaEventRecord(ev[idx], stream);
-}
-
-void ozlu_handle::accumulate_times() {
+void ozlu_handle::phase(int ph) {
     if (!timing) return;
-    cudaEventSynchronize(ev[3]);
-    float a = 0, b = 0, c = 0;
-    cudaEventElapsedTime(&a, ev[0], ev[1]);
-    cudaEventElapsedTime(&b, ev[1], ev[2]);
-    cudaEventElapsedTime(&c, ev[2], ev[3]);
-    stats.convert_ms += a;
-    stats.gemm_ms += b;
-    stats.crt_ms += c;
+    if (open_phase >= 0) {
+        if (pool_used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        cudaEvent_t end = pool[pool_used++];
+        cudaEventRecord(end, stream);
+        marks.push_back({open_phase, {open_ev, end}});
+    }
+    open_phase = ph;
+    if (ph >= 0) {
+        if (pool_used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        open_ev = pool[pool_used++];
+        cudaEventRecord(open_ev, stream);
+    }
 }
 
+void ozlu_handle::resolve_times() {
+    if (marks.empty()) return;
+    cudaEventSynchronize(marks.back().second.second);
+    for (auto& mk : marks) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, mk.second.first, mk.second.second);
+        double* dst[] = {&stats.convert_ms, &stats.gemm_ms, &stats.crt_ms, &stats.panel_ms,
+                         &stats.other_ms};
+        *dst[mk.first] += ms;
+    }
+    marks.clear();
+    pool_used = open_phase >= 0 ? pool_used : 0;
+}
 
 using namespace ozlu;
 
@@ -158,12 +184,6 @@ int ozlu_create(ozlu_handle** handle, void* stream) {
     ozlu_handle* h = new ozlu_handle();
     h->device = dev;
     h->stream = (cudaStream_t)stream;
-    for (auto& e : h->ev)
-        if (cudaEventCreate(&e) != cudaSuccess) {
-            cudaGetLastError();
-            delete h;
-            return OZLU_ERR_CUDA;
-        }
     *handle = h;
     return OZLU_OK;
 }
@@ -174,7 +194,7 @@ int ozlu_destroy(ozlu_handle* h) {
     h->ws.release();
     h->stage.release();
     if (h->lu_scratch) cudaFree(h->lu_scratch);
-    for (auto& e : h->ev) cudaEventDestroy(e);
+    for (auto& e : h->pool) cudaEventDestroy(e);
     delete h;
     return OZLU_OK;
 }
@@ -187,6 +207,8 @@ int ozlu_set_stream(ozlu_handle* h, void* stream) {
 
 int ozlu_set_timing(ozlu_handle* h, int enable) {
     if (!h) return -1;
+    h->phase(-1);
+    h->resolve_times();
     h->timing = enable != 0;
     memset(&h->stats, 0, sizeof h->stats);
     return OZLU_OK;
@@ -195,6 +217,7 @@ int ozlu_set_timing(ozlu_handle* h, int enable) {
 int ozlu_get_stats(ozlu_handle* h, ozlu_stats* out) {
     if (!h) return -1;
     if (!out) return -2;
+    h->resolve_times();
     *out = h->stats;
     return OZLU_OK;
 }

@@ -269,7 +269,9 @@ template <int N>
 void trsm_rec(Ctx& c, long long r, int b, long long j0, int ncols, bool lower) {
     if (c.rc || ncols <= 0) return;
     if (b <= BASE) {
+        c.h->phase(PH_PANEL);
         trsm_base<N>(at(c, r, r), c.lda, at(c, r, j0), c.lda, b, ncols, lower ? 1 : 0, c.h->stream);
+        c.h->count(1);
         return;
     }
     const int b1 = b / 2;
@@ -293,6 +295,9 @@ void panel_rec(Ctx& c, int r, int b, int p0, int p1) {
     if (c.rc) return;
     cudaStream_t s = c.h->stream;
     if (b <= BASE) {
+        c.h->phase(PH_PANEL);
+        c.h->count(2 * b);
+        c.h->stats.panel_launches += 2 * b;
         for (int col = r; col < r + b; ++col) {
             const int rows = c.n - col;
             const int blocks = rows > PIV_THREADS * PIV_BLOCKS ? PIV_BLOCKS
@@ -320,9 +325,10 @@ int getrf_device(ozlu_handle* h, int p, int n, double* A, long long lda, int* ip
     cudaStream_t s = h->stream;
     for (int r0 = 0; r0 < n && !c.rc; r0 += nb) {
         const int b = nb < n - r0 ? nb : n - r0;
-        h->tic(0);
         panel_rec<N>(c, r0, b, r0, r0 + b);
         // (P2) interchanges on the columns left and right of the panel
+        h->phase(PH_OTHER);
+        h->count((r0 > 0) + (r0 + b < n));
         if (r0 > 0) laswp_kernel<N><<<(r0 + 127) / 128, 128, 0, s>>>(A, lda, 0, r0, r0, r0 + b, ipiv);
         if (r0 + b < n)
             laswp_kernel<N><<<(n - r0 - b + 127) / 128, 128, 0, s>>>(A, lda, r0 + b, n, r0, r0 + b, ipiv);
@@ -335,6 +341,7 @@ int getrf_device(ozlu_handle* h, int p, int n, double* A, long long lda, int* ip
                                    at(c, r0, r0 + b), lda, 1, at(c, r0 + b, r0 + b), lda, opts);
         }
     }
+    h->phase(-1);
     if (!c.rc && cudaGetLastError() != cudaSuccess) c.rc = OZLU_ERR_CUDA;
     return c.rc;
 }
@@ -347,6 +354,8 @@ int getrs_device(ozlu_handle* h, int p, int n, int nrhs, double* LU, long long l
     int rc = 0;
     auto L = [&](long long i, long long j) { return LU + (i + j * lda) * N; };
     auto X = [&](long long i) { return B + i * N; };
+    h->phase(PH_PANEL);
+    h->count(1 + 2 * ((n + BASE - 1) / BASE));
     for (int r = 0; r < n && !rc; r += BASE) {
         const int b = BASE < n - r ? BASE : n - r;
         trsm_base<N>(L(r, r), lda, X(r), ldb, b, nrhs, 1, s);
@@ -361,6 +370,7 @@ int getrs_device(ozlu_handle* h, int p, int n, int nrhs, double* LU, long long l
         if (r > 0)
             rc = gemm_device(h, N, p, r, nrhs, b, -1, L(0, r), lda, X(r), ldb, 1, X(0), ldb, opts);
     }
+    h->phase(-1);
     if (!rc && cudaGetLastError() != cudaSuccess) rc = OZLU_ERR_CUDA;
     return rc;
 }

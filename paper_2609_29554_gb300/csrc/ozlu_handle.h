@@ -3,6 +3,8 @@
 
 #include <map>
 #include <tuple>
+#include <utility>
+#include <vector>
 
 #include "ozlu_internal.h"
 
@@ -37,11 +39,19 @@ struct ozlu_handle {
     ozlu::GemmLayout last;
     bool timing = false;
     ozlu_stats stats = {};
-    cudaEvent_t ev[4] = {};
     void* lu_scratch = nullptr;  // pivot-search scratch of ozlu_getrf
-    void tic(int idx);
-    void accumulate_times();
+    // phase timing: (phase, start, end) event triples resolved in ozlu_get_stats
+    std::vector<cudaEvent_t> pool;
+    size_t pool_used = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> marks;
+    int open_phase = -1;
+    cudaEvent_t open_ev = nullptr;
+    void phase(int ph);     // close the open phase (if any) and open ph (-1: none)
+    void resolve_times();
+    void count(long long launches) { stats.launches += launches; }
 };
+
+enum { PH_CONVERT = 0, PH_GEMM = 1, PH_CRT = 2, PH_PANEL = 3, PH_OTHER = 4 };
 
 namespace ozlu {
 int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, const double* A,

@@ -46,7 +46,9 @@ class ozlu_stats(ctypes.Structure):
     _fields_ = [("convert_ms", ctypes.c_double), ("gemm_ms", ctypes.c_double),
                 ("crt_ms", ctypes.c_double), ("panel_ms", ctypes.c_double),
                 ("other_ms", ctypes.c_double), ("gemm_launches", ctypes.c_longlong),
-                ("crt_launches", ctypes.c_longlong), ("panel_launches", ctypes.c_longlong)]
+                ("crt_launches", ctypes.c_longlong), ("panel_launches", ctypes.c_longlong),
+                ("launches", ctypes.c_longlong), ("gemm_ops", ctypes.c_double),
+                ("crt_bytes", ctypes.c_double), ("convert_bytes", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p

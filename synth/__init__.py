@@ -12,9 +12,14 @@ arguments (numpy default_rng seeds).
                       component from exact rationals
   lotkin_rhs          b = A * ones formed exactly from the rational matrix,
                       then rounded
+  prescribed_cond_expansions
+                      A = U diag(sigma) V^T with U, V from the QR of seeded
+                      N(0, 1) matrices and sigma geometric from 1 to 10^-c,
+                      formed exactly (synth/prescribed.py)
 """
 from .matrices import (lotkin_expansions, lotkin_rhs, random_expansions,
                        rational_to_expansion)
+from .prescribed import prescribed_cond_expansions
 
 __all__ = ["random_expansions", "lotkin_expansions", "lotkin_rhs",
-           "rational_to_expansion"]
+           "rational_to_expansion", "prescribed_cond_expansions"]
