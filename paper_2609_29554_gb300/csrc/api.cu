@@ -194,6 +194,7 @@ int ozlu_destroy(ozlu_handle* h) {
     h->ws.release();
     h->stage.release();
     if (h->lu_scratch) cudaFree(h->lu_scratch);
+    if (h->coop_scratch) cudaFree(h->coop_scratch);
     for (auto& e : h->pool) cudaEventDestroy(e);
     delete h;
     return OZLU_OK;

@@ -19,6 +19,7 @@
 #include <string.h>
 
 #include "expansion.cuh"
+#include "mpf.cuh"
 #include "ozlu_handle.h"
 
 namespace ozlu {
@@ -27,17 +28,41 @@ namespace {
 constexpr int BASE = 32;        // base-block width of the recursion
 constexpr int PIV_THREADS = 256;
 constexpr int PIV_BLOCKS = 152;
+constexpr int MAXPART = 1024;   // block partials of a column step
+constexpr int STEP_ROWS = 16;   // rows per block of a column step
+
+// limbs of the panel arithmetic: 32 L >= 53 nc + 22
+template <int N>
+struct Limbs { static constexpr int L = N == 2 ? 4 : (N == 3 ? 6 : 8); };
 
 struct LuScratch {
-    double recip[4];
-    double pivot[4];
+    uint32_t rm[8];             // reciprocal of the current pivot (MPF words)
+    int re, rneg;
     int piv;
     int zero;
     unsigned int counter;
     int info;
-    double pval[PIV_BLOCKS][4];
-    int pidx[PIV_BLOCKS];
+    double pval[MAXPART][4];    // block candidates (expansion values)
+    int pidx[MAXPART];
 };
+
+template <int L>
+__device__ __forceinline__ void put_recip(LuScratch* sc, const MPF<L>& r) {
+#pragma unroll
+    for (int i = 0; i < L; ++i) sc->rm[i] = r.m[i];
+    sc->re = r.e;
+    sc->rneg = r.neg;
+}
+
+template <int L>
+__device__ __forceinline__ MPF<L> get_recip(const LuScratch* sc) {
+    MPF<L> r;
+#pragma unroll
+    for (int i = 0; i < L; ++i) r.m[i] = sc->rm[i];
+    r.e = sc->re;
+    r.neg = sc->rneg;
+    return r;
+}
 
 __device__ __forceinline__ double* elem(double* A, long long lda, int nc, long long i, long long j) {
     return A + (i + j * lda) * nc;
@@ -50,6 +75,47 @@ __device__ __forceinline__ bool better(const Exp<N>& a, int ia, const Exp<N>& b,
     if (ia < 0) return false;
     const int c = abs_cmp<N>(a, b);
     return c > 0 || (c == 0 && ia < ib);
+}
+
+// Last-block reduction of the block candidates: each thread scans a strided
+// share of the partials, then a shared-memory tree keeps the best (largest
+// magnitude, first index on ties).  All threads of the block must call it;
+// the result is valid in thread 0.
+template <int N, int THREADS>
+__device__ __forceinline__ void reduce_partials(const LuScratch* sc, int nparts, Exp<N>& b, int& ib) {
+    __shared__ double rv[THREADS][N];
+    __shared__ int ri[THREADS];
+    Exp<N> best;
+    int bi = -1;
+#pragma unroll
+    for (int q = 0; q < N; ++q) best.x[q] = 0.0;
+    for (int k = threadIdx.x; k < nparts; k += THREADS) {
+        Exp<N> v;
+#pragma unroll
+        for (int q = 0; q < N; ++q) v.x[q] = ((volatile const double*)sc->pval[k])[q];
+        const int iv = ((volatile const int*)sc->pidx)[k];
+        if (better<N>(v, iv, best, bi)) { best = v; bi = iv; }
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) rv[threadIdx.x][q] = best.x[q];
+    ri[threadIdx.x] = bi;
+    __syncthreads();
+    for (int s = THREADS / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            Exp<N> u, v;
+#pragma unroll
+            for (int q = 0; q < N; ++q) { u.x[q] = rv[threadIdx.x][q]; v.x[q] = rv[threadIdx.x + s][q]; }
+            if (better<N>(v, ri[threadIdx.x + s], u, ri[threadIdx.x])) {
+#pragma unroll
+                for (int q = 0; q < N; ++q) rv[threadIdx.x][q] = v.x[q];
+                ri[threadIdx.x] = ri[threadIdx.x + s];
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < N; ++q) b.x[q] = rv[0][q];
+    ib = ri[0];
 }
 
 // Pivot search of column c over rows [c, n); the last block to finish reduces
@@ -99,18 +165,10 @@ __global__ void __launch_bounds__(PIV_THREADS) pivot_kernel(double* A, long long
     if (!last) return;
     __threadfence();
     __shared__ int piv;
+    Exp<N> b;
+    int ib;
+    reduce_partials<N, PIV_THREADS>(sc, gridDim.x, b, ib);
     if (threadIdx.x == 0) {
-        Exp<N> b;
-        int ib = -1;
-#pragma unroll
-        for (int q = 0; q < N; ++q) b.x[q] = 0.0;
-        for (int k = 0; k < (int)gridDim.x; ++k) {
-            Exp<N> v;
-#pragma unroll
-            for (int q = 0; q < N; ++q) v.x[q] = ((volatile double*)sc->pval[k])[q];
-            const int iv = ((volatile int*)sc->pidx)[k];
-            if (better<N>(v, iv, b, ib)) { b = v; ib = iv; }
-        }
         if (ib < 0) ib = c;
         piv = ib;
         sc->piv = ib;
@@ -120,12 +178,8 @@ __global__ void __launch_bounds__(PIV_THREADS) pivot_kernel(double* A, long long
         sc->zero = zero ? 1 : 0;
         if (zero && sc->info == 0) sc->info = c + 1;
         if (!zero) {
-            Exp<N> one;
-            one.x[0] = 1.0;
-#pragma unroll
-            for (int q = 1; q < N; ++q) one.x[q] = 0.0;
-            Exp<N> r = div<N>(one, b);
-            store<N>(sc->recip, r);
+            constexpr int L = Limbs<N>::L;
+            put_recip<L>(sc, mpf_recip<L>(mpf_from_exp<L, N>(b.x)));
         }
     }
     __syncthreads();
@@ -140,30 +194,335 @@ __global__ void __launch_bounds__(PIV_THREADS) pivot_kernel(double* A, long long
     }
 }
 
-// Rows i in (c, n): l_i = a_ic / pivot (times the reciprocal), then
-// a_ik -= l_i a_ck for k in (c, c1).
+// One column step of a base block, fused with the next pivot search.
+// Rows i in (c, n): l_i = a_ic * (1 / pivot), a_ik -= l_i a_ck for k in (c, c1),
+// all in L-limb integer floating point; each block then offers its best
+// candidate for column c + 1 and the last block to finish reduces them,
+// interchanges rows c + 1 and piv over the outer panel columns [p0, p1),
+// records ipiv and the reciprocal of the new pivot.
 template <int N>
-__global__ void __launch_bounds__(128) scale_update_kernel(double* A, long long lda, int n, int c,
-                                                           int c1, const LuScratch* sc) {
-    __shared__ double urow[BASE][N];
+__global__ void __launch_bounds__(128) column_step_kernel(double* A, long long lda, int n, int c,
+                                                          int c1, int p0, int p1, int* ipiv,
+                                                          LuScratch* sc) {
+    constexpr int L = Limbs<N>::L;
+    __shared__ MPF<L> urow[BASE];
+    __shared__ MPF<L> lrow[STEP_ROWS];
+    __shared__ double cand[STEP_ROWS][N];
+    __shared__ int candi[STEP_ROWS];
+    __shared__ bool last;
+    __shared__ int piv;
     const int cols = c1 - c - 1;
+    const bool zero = sc->zero != 0;
     for (int k = threadIdx.x; k < cols; k += blockDim.x)
+        urow[k] = mpf_from_exp<L, N>(elem(A, lda, N, c, c + 1 + k));
+    // candidate of this thread (threads < STEP_ROWS) over its rows of all chunks
+    Exp<N> best;
+    int bi = -1;
 #pragma unroll
-        for (int q = 0; q < N; ++q) urow[k][q] = elem(A, lda, N, c, c + 1 + k)[q];
+    for (int q = 0; q < N; ++q) best.x[q] = 0.0;
+    const int nchunks = (n - c - 1 + STEP_ROWS - 1) / STEP_ROWS;
+    for (int chunk = blockIdx.x; chunk < nchunks; chunk += gridDim.x) {
+        const int i0 = c + 1 + chunk * STEP_ROWS;
+        __syncthreads();
+        if (threadIdx.x < STEP_ROWS) {
+            const int i = i0 + threadIdx.x;
+            if (i < n && !zero) {
+                double* ai = elem(A, lda, N, i, c);
+                MPF<L> l = mpf_mul<L>(mpf_from_exp<L, N>(ai), get_recip<L>(sc));
+                mpf_to_exp<L, N>(l, ai);
+                lrow[threadIdx.x] = l;
+            }
+        }
+        __syncthreads();
+        if (!zero) {
+            for (int pidx = threadIdx.x; pidx < STEP_ROWS * cols; pidx += blockDim.x) {
+                const int k = pidx / STEP_ROWS, rr = pidx - k * STEP_ROWS;
+                const int i = i0 + rr;
+                if (i >= n) continue;
+                double* a = elem(A, lda, N, i, c + 1 + k);
+                mpf_to_exp<L, N>(mpf_fms<L>(mpf_from_exp<L, N>(a), lrow[rr], urow[k]), a);
+            }
+        }
+        if (cols > 0) {
+            __syncthreads();
+            if (threadIdx.x < STEP_ROWS) {
+                const int i = i0 + threadIdx.x;
+                if (i < n) {
+                    const Exp<N> v = load<N>(elem(A, lda, N, i, c + 1));
+                    if (better<N>(v, i, best, bi)) { best = v; bi = i; }
+                }
+            }
+        }
+    }
+    if (cols == 0) return;  // last column of the base block: no next pivot here
+    if (threadIdx.x < STEP_ROWS) {
+#pragma unroll
+        for (int q = 0; q < N; ++q) cand[threadIdx.x][q] = best.x[q];
+        candi[threadIdx.x] = bi;
+    }
     __syncthreads();
-    if (sc->zero) return;
-    const int i = c + 1 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const Exp<N> r = load<N>(sc->recip);
-    double* ai = elem(A, lda, N, i, c);
-    const Exp<N> l = mul<N>(load<N>(ai), r);
-    store<N>(ai, l);
-    for (int k = 0; k < cols; ++k) {
-        Exp<N> u;
+    if (threadIdx.x == 0) {
+        Exp<N> b;
+        int ib = -1;
 #pragma unroll
-        for (int q = 0; q < N; ++q) u.x[q] = urow[k][q];
-        double* a = elem(A, lda, N, i, c + 1 + k);
-        store<N>(a, fms<N>(load<N>(a), l, u));
+        for (int q = 0; q < N; ++q) b.x[q] = 0.0;
+        for (int r = 0; r < STEP_ROWS; ++r) {
+            Exp<N> v;
+#pragma unroll
+            for (int q = 0; q < N; ++q) v.x[q] = cand[r][q];
+            if (better<N>(v, candi[r], b, ib)) { b = v; ib = candi[r]; }
+        }
+#pragma unroll
+        for (int q = 0; q < N; ++q) sc->pval[blockIdx.x][q] = b.x[q];
+        sc->pidx[blockIdx.x] = ib;
+        __threadfence();
+        const unsigned int done = atomicAdd(&sc->counter, 1u);
+        last = done == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!last) return;
+    __threadfence();
+    const int cn = c + 1;
+    Exp<N> b;
+    int ib;
+    reduce_partials<N, 128>(sc, gridDim.x, b, ib);
+    if (threadIdx.x == 0) {
+        if (ib < 0) ib = cn;
+        piv = ib;
+        ipiv[cn] = ib + 1;
+        sc->counter = 0;
+        const bool z = b.x[0] == 0.0;
+        sc->zero = z ? 1 : 0;
+        if (z && sc->info == 0) sc->info = cn + 1;
+        if (!z) put_recip<L>(sc, mpf_recip<L>(mpf_from_exp<L, N>(b.x)));
+    }
+    __syncthreads();
+    const int pv = piv;
+    if (pv != cn) {
+        for (int j = p0 + threadIdx.x; j < p1; j += blockDim.x) {
+            double* a = elem(A, lda, N, cn, j);
+            double* b = elem(A, lda, N, pv, j);
+#pragma unroll
+            for (int q = 0; q < N; ++q) { const double t = a[q]; a[q] = b[q]; b[q] = t; }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Cooperative factorisation of one base block: columns [c0, c0 + b) over rows
+// [c0, n).  One block per SM owns a contiguous slice of rows and keeps its
+// b-column slice in shared memory as L-limb floats for the whole block, so a
+// column step costs one grid barrier: each block publishes its best candidate
+// row for the next column (value, index and the whole row), every block
+// reduces the same partials to the pivot, takes the pivot row from the
+// winner's slot, applies the interchange to its rows, scales and updates.
+// The grid barrier spins with an iteration limit; on expiry the kernel records
+// OZLU_ERR_TIMEOUT in the scratch and returns.
+constexpr int COOP_MAXG = 304;           // blocks (up to 2 per SM)
+constexpr int COOP_THREADS = 128;
+constexpr long long BARRIER_SPIN_LIMIT = 20000000;  // ~2 s with 100 ns naps
+
+template <int L>
+struct CoopSlot {
+    MPF<L> row[BASE];   // candidate row (all b columns)
+    int idx;            // its global row index, -1 if none
+};
+
+template <int L>
+struct CoopScratch {
+    unsigned int bar_count;
+    unsigned int bar_gen;
+    int error;
+    int pad;
+    CoopSlot<L> part[2][COOP_MAXG];  // double-buffered by column parity
+    MPF<L> orow[2][BASE];            // old row c, for the owner of the pivot row
+};
+
+template <int L>
+__device__ __forceinline__ bool grid_barrier(CoopScratch<L>* sc) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned int* genp = &sc->bar_gen;
+        const unsigned int gen = *genp;
+        __threadfence();
+        const unsigned int arrived = atomicAdd(&sc->bar_count, 1u) + 1u;
+        if (arrived == gridDim.x) {
+            sc->bar_count = 0;
+            __threadfence();
+            atomicAdd(&sc->bar_gen, 1u);
+        } else {
+            long long spins = 0;
+            while (*genp == gen) {
+                if (++spins > BARRIER_SPIN_LIMIT) {
+                    atomicExch(&sc->error, OZLU_ERR_TIMEOUT);
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int*)&sc->error == 0;
+}
+
+// load an L-limb float written by another block (bypassing L1)
+template <int L>
+__device__ __forceinline__ MPF<L> ld_cg(const MPF<L>* p) {
+    MPF<L> v;
+    const unsigned int* w = reinterpret_cast<const unsigned int*>(p);
+#pragma unroll
+    for (int i = 0; i < L; ++i) v.m[i] = __ldcg(w + i);
+    v.e = __ldcg(reinterpret_cast<const int*>(w + L));
+    v.neg = __ldcg(reinterpret_cast<const int*>(w + L + 1));
+    return v;
+}
+
+// |a| > |b|, or equal and ia < ib (first index on ties); ib < 0: b is empty
+template <int L>
+__device__ __forceinline__ bool mpf_better(const MPF<L>& a, int ia, const MPF<L>& b, int ib) {
+    if (ia < 0) return false;
+    if (ib < 0) return true;
+    const int c = mpf_abs_cmp<L>(a, b);
+    return c > 0 || (c == 0 && ia < ib);
+}
+
+template <int N>
+__global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
+    double* A, long long lda, int n, int c0, int b, int p0, int p1, int rows_per_block,
+    int* ipiv, int* info, CoopScratch<Limbs<N>::L>* sc) {
+    constexpr int L = Limbs<N>::L;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    MPF<L>* a = reinterpret_cast<MPF<L>*>(smraw);  // [r][k], r < rows_per_block, k < b
+    __shared__ MPF<L> prow[BASE];
+    __shared__ MPF<L> rec;
+    __shared__ int s_piv, s_widx;
+    __shared__ MPF<L> cv[COOP_THREADS];
+    __shared__ int ci[COOP_THREADS];
+    const int g = blockIdx.x, G = gridDim.x, tid = threadIdx.x;
+    const int r0 = c0 + g * rows_per_block;
+    const int r1 = min(n, r0 + rows_per_block);
+    const int nr = max(0, r1 - r0);
+    auto owner = [&](int row) { return (row - c0) / rows_per_block; };
+
+    for (int p = tid; p < nr * b; p += COOP_THREADS) {
+        const int r = p / b, k = p - r * b;
+        a[r * b + k] = mpf_from_exp<L, N>(elem(A, lda, N, r0 + r, c0 + k));
+    }
+    __syncthreads();
+
+    // candidate of this block for local column kc among rows >= row_lo
+    auto publish = [&](int kc, int row_lo) {
+        MPF<L> best = mpf_make_zero<L>();
+        int bi = -1;
+        for (int r = tid; r < nr; r += COOP_THREADS) {
+            const int i = r0 + r;
+            if (i < row_lo) continue;
+            if (mpf_better<L>(a[r * b + kc], i, best, bi)) { best = a[r * b + kc]; bi = i; }
+        }
+        cv[tid] = best;
+        ci[tid] = bi;
+        __syncthreads();
+        for (int s = COOP_THREADS / 2; s > 0; s >>= 1) {
+            if (tid < s && mpf_better<L>(cv[tid + s], ci[tid + s], cv[tid], ci[tid])) {
+                cv[tid] = cv[tid + s];
+                ci[tid] = ci[tid + s];
+            }
+            __syncthreads();
+        }
+        CoopSlot<L>& slot = sc->part[kc & 1][g];
+        const int wi = ci[0];
+        if (tid == 0) slot.idx = wi;
+        if (wi >= 0)
+            for (int k = tid; k < b; k += COOP_THREADS) slot.row[k] = a[(wi - r0) * b + k];
+        __syncthreads();
+    };
+
+    publish(0, c0);
+    for (int kc = 0; kc < b; ++kc) {
+        const int c = c0 + kc;
+        // the owner of row c leaves its old contents for the pivot row's owner
+        if (owner(c) == g)
+            for (int k = tid; k < b; k += COOP_THREADS) sc->orow[kc & 1][k] = a[(c - r0) * b + k];
+        if (!grid_barrier<L>(sc)) return;
+        // every block reduces the same partials to the same pivot
+        {
+            MPF<L> best = mpf_make_zero<L>();
+            int bi = -1, bw = -1;
+            for (int q = tid; q < G; q += COOP_THREADS) {
+                const CoopSlot<L>& slot = sc->part[kc & 1][q];
+                const int iv = __ldcg(&slot.idx);
+                if (iv < 0) continue;
+                const MPF<L> v = ld_cg<L>(&slot.row[kc]);
+                if (mpf_better<L>(v, iv, best, bi)) { best = v; bi = iv; bw = q; }
+            }
+            cv[tid] = best;
+            ci[tid] = bi;
+            __shared__ int cw[COOP_THREADS];
+            cw[tid] = bw;
+            __syncthreads();
+            for (int s = COOP_THREADS / 2; s > 0; s >>= 1) {
+                if (tid < s && mpf_better<L>(cv[tid + s], ci[tid + s], cv[tid], ci[tid])) {
+                    cv[tid] = cv[tid + s];
+                    ci[tid] = ci[tid + s];
+                    cw[tid] = cw[tid + s];
+                }
+                __syncthreads();
+            }
+            if (tid == 0) {
+                s_piv = ci[0] < 0 ? c : ci[0];
+                s_widx = cw[0];
+            }
+            __syncthreads();
+        }
+        const int piv = s_piv;
+        // new row c = the pivot row
+        for (int k = tid; k < b; k += COOP_THREADS)
+            prow[k] = s_widx >= 0 ? ld_cg<L>(&sc->part[kc & 1][s_widx].row[k]) : mpf_make_zero<L>();
+        __syncthreads();
+        const bool zero = mpf_zero<L>(prow[kc]);
+        if (g == 0 && tid == 0) {
+            ipiv[c] = piv + 1;
+            if (zero && *info == 0) *info = c + 1;
+        }
+        if (!zero && piv != c) {
+            if (owner(c) == g)
+                for (int k = tid; k < b; k += COOP_THREADS) a[(c - r0) * b + k] = prow[k];
+            if (owner(piv) == g)
+                for (int k = tid; k < b; k += COOP_THREADS) a[(piv - r0) * b + k] = ld_cg<L>(&sc->orow[kc & 1][k]);
+            // interchange the rest of the outer panel (global, expansion format)
+            if (g == 0) {
+                const int span = (c0 - p0) + (p1 - c0 - b);
+                for (int t = tid; t < span; t += COOP_THREADS) {
+                    const int j = t < c0 - p0 ? p0 + t : c0 + b + (t - (c0 - p0));
+                    double* x = elem(A, lda, N, c, j);
+                    double* y = elem(A, lda, N, piv, j);
+#pragma unroll
+                    for (int q = 0; q < N; ++q) { const double tt = x[q]; x[q] = y[q]; y[q] = tt; }
+                }
+            }
+        }
+        if (tid == 0 && !zero) rec = mpf_recip<L>(prow[kc]);
+        __syncthreads();
+        if (!zero) {
+            // multipliers and the rank-1 update of this block's rows below c
+            const int lo = max(r0, c + 1) - r0;
+            for (int r = lo + tid; r < nr; r += COOP_THREADS)
+                a[r * b + kc] = mpf_mul<L>(a[r * b + kc], rec);
+            __syncthreads();
+            const int cols = b - kc - 1;
+            const int rows = nr - lo;
+            for (int p = tid; p < rows * cols; p += COOP_THREADS) {
+                const int r = lo + p / cols, k = kc + 1 + (p - (p / cols) * cols);
+                a[r * b + k] = mpf_fms<L>(a[r * b + k], a[r * b + kc], prow[k]);
+            }
+        }
+        __syncthreads();
+        if (kc + 1 < b) publish(kc + 1, c + 1);
+    }
+    for (int p = tid; p < nr * b; p += COOP_THREADS) {
+        const int r = p / b, k = p - r * b;
+        mpf_to_exp<L, N>(a[r * b + k], elem(A, lda, N, r0 + r, c0 + k));
     }
 }
 
@@ -185,70 +544,96 @@ __global__ void laswp_kernel(double* A, long long lda, int j0, int j1, int k0, i
 }
 
 // X <- L^-1 X for a unit lower (lower = 1) or U^-1 X for an upper (lower = 0,
-// non-unit) b x b triangle, b <= BASE; X is b x ncols.  A block holds 32
-// columns; thread (tx, ty) owns column tx and rows ty, ty + 8, ...
+// non-unit) b x b triangle, b <= BASE; X is b x ncols.  L-limb integer
+// floating point; a block of 32 x cpb threads owns cpb columns, thread
+// (row, column) updates its element after each pivot row is final.
 template <int N>
 __global__ void __launch_bounds__(256) trsm_base_kernel(const double* T, long long ldt, double* X,
                                                         long long ldx, int b, int ncols, int lower) {
-    extern __shared__ double sm[];
-    double* sl = sm;                       // b x b triangle, [i][k][q]
-    double* sx = sm + BASE * BASE * N;     // b x 32 block of X, [i][col][q]
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int col = blockIdx.x * 32 + tx;
+    constexpr int L = Limbs<N>::L;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    MPF<L>* sl = reinterpret_cast<MPF<L>*>(smraw);   // [i][k]
+    MPF<L>* rd = sl + BASE * BASE;                   // reciprocal diagonal (upper)
+    MPF<L>* sx = rd + BASE;                          // [cc][i]
+    const int cpb = blockDim.x >> 5;
+    const int row = threadIdx.x & 31, cc = threadIdx.x >> 5;
+    const int col = blockIdx.x * cpb + cc;
     for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
-        const int i = idx / b, k = idx % b;
-#pragma unroll
-        for (int q = 0; q < N; ++q) sl[(i * BASE + k) * N + q] = T[((long long)i + (long long)k * ldt) * N + q];
+        const int i = idx / b, k = idx - i * b;
+        const bool need = lower ? (k < i) : (k >= i);
+        sl[i * BASE + k] = need ? mpf_from_exp<L, N>(T + ((long long)i + (long long)k * ldt) * N)
+                                : mpf_make_zero<L>();
     }
-    for (int i = ty; i < b; i += 8)
-#pragma unroll
-        for (int q = 0; q < N; ++q)
-            sx[(i * 32 + tx) * N + q] = col < ncols ? X[((long long)i + (long long)col * ldx) * N + q] : 0.0;
+    __syncthreads();
+    if (!lower)
+        for (int k = threadIdx.x; k < b; k += blockDim.x)
+            rd[k] = mpf_zero<L>(sl[k * BASE + k]) ? mpf_make_zero<L>() : mpf_recip<L>(sl[k * BASE + k]);
+    if (row < b)
+        sx[cc * BASE + row] = col < ncols ? mpf_from_exp<L, N>(X + ((long long)row + (long long)col * ldx) * N)
+                                          : mpf_make_zero<L>();
     __syncthreads();
     for (int s = 0; s < b; ++s) {
         const int k = lower ? s : b - 1 - s;
-        if (!lower && ty == 0) {
-            // x_k /= u_kk
-            Exp<N> d, x;
-#pragma unroll
-            for (int q = 0; q < N; ++q) { d.x[q] = sl[(k * BASE + k) * N + q]; x.x[q] = sx[(k * 32 + tx) * N + q]; }
-            if (d.x[0] != 0.0) x = div<N>(x, d);
-#pragma unroll
-            for (int q = 0; q < N; ++q) sx[(k * 32 + tx) * N + q] = x.x[q];
+        if (!lower) {
+            if (row == k) sx[cc * BASE + k] = mpf_mul<L>(sx[cc * BASE + k], rd[k]);
+            __syncthreads();
         }
-        __syncthreads();
-        Exp<N> xk;
-#pragma unroll
-        for (int q = 0; q < N; ++q) xk.x[q] = sx[(k * 32 + tx) * N + q];
-        for (int i = ty; i < b; i += 8) {
-            if ((lower && i > k) || (!lower && i < k)) {
-                Exp<N> lik, xi;
-#pragma unroll
-                for (int q = 0; q < N; ++q) { lik.x[q] = sl[(i * BASE + k) * N + q]; xi.x[q] = sx[(i * 32 + tx) * N + q]; }
-                xi = fms<N>(xi, lik, xk);
-#pragma unroll
-                for (int q = 0; q < N; ++q) sx[(i * 32 + tx) * N + q] = xi.x[q];
-            }
-        }
+        if (row < b && ((lower && row > k) || (!lower && row < k)))
+            sx[cc * BASE + row] = mpf_fms<L>(sx[cc * BASE + row], sl[row * BASE + k], sx[cc * BASE + k]);
         __syncthreads();
     }
-    if (col < ncols)
-        for (int i = ty; i < b; i += 8)
-#pragma unroll
-            for (int q = 0; q < N; ++q) X[((long long)i + (long long)col * ldx) * N + q] = sx[(i * 32 + tx) * N + q];
+    if (row < b && col < ncols) mpf_to_exp<L, N>(sx[cc * BASE + row], X + ((long long)row + (long long)col * ldx) * N);
 }
 
 template <int N>
 void trsm_base(const double* T, long long ldt, double* X, long long ldx, int b, int ncols, int lower,
                cudaStream_t s) {
     if (ncols <= 0 || b <= 0) return;
-    const size_t smem = sizeof(double) * N * (BASE * BASE + BASE * 32);
+    constexpr int L = Limbs<N>::L;
+    int cpb = ncols / 304;
+    cpb = cpb < 1 ? 1 : (cpb > 8 ? 8 : cpb);
+    const size_t smem = sizeof(MPF<L>) * (BASE * BASE + BASE + BASE * cpb);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(trsm_base_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(trsm_base_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(MPF<L>) * (BASE * BASE + BASE + BASE * 8)));
         attr = true;
     }
-    trsm_base_kernel<N><<<(ncols + 31) / 32, 256, smem, s>>>(T, ldt, X, ldx, b, ncols, lower);
+    trsm_base_kernel<N><<<(ncols + cpb - 1) / cpb, 32 * cpb, smem, s>>>(T, ldt, X, ldx, b, ncols, lower);
+}
+
+// Launch the cooperative base-block kernel; returns false when the slice of
+// rows does not fit in shared memory (the caller then uses column kernels).
+template <int N>
+bool base_block_coop(double* A, long long lda, int n, int c0, int b, int p0, int p1, int* ipiv,
+                     int* info, void* scratch, cudaStream_t s) {
+    constexpr int L = Limbs<N>::L;
+    static int sms = 0;
+    if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    for (int per_sm = 1; per_sm <= 2; ++per_sm) {
+        int G = sms * per_sm;
+        if (G > COOP_MAXG) G = COOP_MAXG;
+        const int rows = (n - c0 + G - 1) / G;
+        const size_t smem = sizeof(MPF<L>) * (size_t)rows * b;
+        if (smem > 200 * 1024 / per_sm) continue;
+        cudaFuncSetAttribute(base_block_coop_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(smem < 1024 ? 1024 : smem));
+        int active = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&active, base_block_coop_kernel<N>, COOP_THREADS,
+                                                      smem);
+        if (active * sms < G) continue;
+        auto* sc = reinterpret_cast<CoopScratch<L>*>(scratch);
+        void* args[] = {&A, &lda, &n, &c0, &b, &p0, &p1, (void*)&rows, &ipiv, &info, &sc};
+        int rows_arg = rows;
+        args[7] = &rows_arg;
+        if (cudaLaunchCooperativeKernel((void*)base_block_coop_kernel<N>, G, COOP_THREADS, args, smem, s) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return true;
+    }
+    return false;
 }
 
 struct Ctx {
@@ -296,16 +681,26 @@ void panel_rec(Ctx& c, int r, int b, int p0, int p1) {
     cudaStream_t s = c.h->stream;
     if (b <= BASE) {
         c.h->phase(PH_PANEL);
-        c.h->count(2 * b);
-        c.h->stats.panel_launches += 2 * b;
-        for (int col = r; col < r + b; ++col) {
-            const int rows = c.n - col;
+        if (base_block_coop<N>(c.A, c.lda, c.n, r, b, p0, p1, c.ipiv, &c.sc->info, c.h->coop_scratch, s)) {
+            c.h->count(1);
+            c.h->stats.panel_launches += 1;
+            return;
+        }
+        c.h->count(1 + b);
+        c.h->stats.panel_launches += 1 + b;
+        {
+            const int rows = c.n - r;
             const int blocks = rows > PIV_THREADS * PIV_BLOCKS ? PIV_BLOCKS
                                                                : (rows + PIV_THREADS - 1) / PIV_THREADS;
-            pivot_kernel<N><<<blocks, PIV_THREADS, 0, s>>>(c.A, c.lda, c.n, col, p0, p1, c.ipiv, c.sc);
-            if (rows > 1)
-                scale_update_kernel<N><<<(rows - 1 + 127) / 128, 128, 0, s>>>(c.A, c.lda, c.n, col,
-                                                                              r + b, c.sc);
+            pivot_kernel<N><<<blocks, PIV_THREADS, 0, s>>>(c.A, c.lda, c.n, r, p0, p1, c.ipiv, c.sc);
+        }
+        for (int col = r; col < r + b; ++col) {
+            const int rows = c.n - col - 1;
+            if (rows <= 0) break;
+            int blocks = (rows + STEP_ROWS - 1) / STEP_ROWS;
+            if (blocks > MAXPART) blocks = MAXPART;
+            column_step_kernel<N><<<blocks, 128, 0, s>>>(c.A, c.lda, c.n, col, r + b, p0, p1, c.ipiv,
+                                                          c.sc);
         }
         return;
     }
@@ -386,8 +781,31 @@ int lu_scratch(ozlu_handle* h, LuScratch** out) {
             return OZLU_ERR_NOMEM;
         }
     }
+    if (!h->coop_scratch) {
+        h->coop_bytes = sizeof(CoopScratch<8>);
+        if (cudaMalloc(&h->coop_scratch, h->coop_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            h->coop_scratch = nullptr;
+            return OZLU_ERR_NOMEM;
+        }
+    }
     *out = (LuScratch*)h->lu_scratch;
     return OZLU_OK;
+}
+
+// barrier counters and the error word start at zero for every factorisation
+int coop_reset(ozlu_handle* h, cudaStream_t s) {
+    return cudaMemsetAsync(h->coop_scratch, 0, 4 * sizeof(int), s) == cudaSuccess ? OZLU_OK
+                                                                                   : OZLU_ERR_CUDA;
+}
+
+int coop_error(ozlu_handle* h, cudaStream_t s) {
+    int err = 0;
+    if (cudaMemcpyAsync(&err, (char*)h->coop_scratch + 2 * sizeof(int), sizeof(int),
+                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess)
+        return OZLU_ERR_CUDA;
+    return err;
 }
 
 }  // namespace ozlu
@@ -413,6 +831,7 @@ extern "C" int ozlu_getrf(ozlu_handle* h, int nc, int p, int n, double* A, long 
     int rc = lu_scratch(h, &sc);
     if (rc) return rc;
     if (cudaMemsetAsync(sc, 0, sizeof(LuScratch), s)) return OZLU_ERR_CUDA;
+    if ((rc = coop_reset(h, s))) return rc;
     const bool dA = is_device_ptr(A), dP = is_device_ptr(ipiv), dI = is_device_ptr(info);
     const size_t abytes = sizeof(double) * nc * (size_t)lda * (n ? n : 1);
     double* gA = A;
@@ -434,6 +853,7 @@ extern "C" int ozlu_getrf(ozlu_handle* h, int nc, int p, int n, double* A, long 
         }
     }
     if (rc) return rc;
+    if ((rc = coop_error(h, s))) return rc;
     if (!dA && cudaMemcpyAsync(A, gA, abytes, cudaMemcpyDeviceToHost, s)) return OZLU_ERR_CUDA;
     if (n && gP != ipiv &&
         cudaMemcpyAsync(ipiv, gP, sizeof(int) * n, dP ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s))

@@ -1,0 +1,331 @@
+// Multi-limb binary floating point on 32-bit integer limbs (device).
+//
+// value = (-1)^neg * m * 2^(e - 32 L), with m an L-word magnitude whose top
+// bit is set (normalised), or zero (m = 0).  Every operation rounds its
+// exact (or sticky-truncated) result to L words, round to nearest even.
+// The arithmetic runs on the integer pipes (IMAD), which on GB300 issue
+// about 40 times the binary64 FMA rate; the LU panel uses it for DD/TD/QD
+// elements at 32 L >= 53 nc + 22 bits and converts to and from the
+// expansion format (successive round-to-nearest on the way out).
+#pragma once
+
+#include <stdint.h>
+
+#include "mp_device.cuh"
+
+namespace ozlu {
+
+template <int L>
+struct MPF {
+    uint32_t m[L];
+    int e;
+    int neg;
+};
+
+template <int L>
+__device__ __forceinline__ bool mpf_zero(const MPF<L>& a) {
+    return a.m[L - 1] == 0;
+}
+
+template <int L>
+__device__ __forceinline__ MPF<L> mpf_make_zero() {
+    MPF<L> r;
+#pragma unroll
+    for (int i = 0; i < L; ++i) r.m[i] = 0;
+    r.e = 0;
+    r.neg = 0;
+    return r;
+}
+
+// Round the W-word magnitude X (top word nonzero or all zero) to L words:
+// normalise, keep the top 32 L bits, round to nearest even with a sticky.
+// `ex` is the exponent such that value = X * 2^(ex - 32 W).
+template <int L, int W>
+__device__ __forceinline__ MPF<L> mpf_round(uint32_t (&X)[W], int ex, int neg, bool sticky_in) {
+    MPF<L> r;
+    r.neg = neg;
+    const int bl = bit_length<W>(X);
+    if (bl == 0) {
+        r = mpf_make_zero<L>();
+        return r;
+    }
+    // shift left so that the top bit is bit 32W-1
+    const int sh = 32 * W - bl;
+    if (sh > 0 && sh < 32) {
+        // common case: the top word is nonzero, a funnel shift of every word
+#pragma unroll
+        for (int i = W - 1; i > 0; --i) X[i] = __funnelshift_l(X[i - 1], X[i], sh);
+        X[0] <<= sh;
+    } else if (sh >= 32) {
+        const int q = sh >> 5, rr = sh & 31;
+        uint32_t T[W];
+#pragma unroll
+        for (int i = W - 1; i >= 0; --i) {
+            uint32_t hi = 0, lo = 0;
+#pragma unroll
+            for (int k = 0; k < W; ++k) {
+                if (k == i - q) hi = X[k];
+                if (k == i - q - 1) lo = X[k];
+            }
+            T[i] = rr ? (hi << rr) | (lo >> (32 - rr)) : hi;
+        }
+#pragma unroll
+        for (int i = 0; i < W; ++i) X[i] = T[i];
+    }
+    ex -= sh;
+    // top L words; round bit = top bit of word W-L-1; sticky = the rest
+    bool rbit = false, sticky = sticky_in;
+    if (W > L) {
+        rbit = (X[W - L - 1] >> 31) != 0;
+        sticky |= (X[W - L - 1] & 0x7fffffffu) != 0;
+#pragma unroll
+        for (int i = 0; i < W - L - 1; ++i) sticky |= X[i] != 0;
+    }
+#pragma unroll
+    for (int i = 0; i < L; ++i) r.m[i] = X[W - L + i];
+    // X * 2^(ex - 32 W) with the top L words kept: m * 2^(ex - 32 L)
+    r.e = ex;
+    if (rbit && (sticky || (r.m[0] & 1u))) {
+        uint64_t c = 1;
+#pragma unroll
+        for (int i = 0; i < L; ++i) {
+            const uint64_t s = (uint64_t)r.m[i] + c;
+            r.m[i] = (uint32_t)s;
+            c = s >> 32;
+        }
+        if (c) {  // carried out: 1000...0
+            r.m[L - 1] = 0x80000000u;
+            r.e += 1;
+        }
+    }
+    return r;
+}
+
+// from an expansion of N binary64 components (sticky-truncated to 32(L+2) bits,
+// then rounded to L words)
+template <int L, int N>
+__device__ __forceinline__ MPF<L> mpf_from_exp(const double* x) {
+    constexpr int W = L + 2;
+    if (x[0] == 0.0) return mpf_make_zero<L>();
+    const int top = frexp_exp(x[0]) + 1;  // |value| < 2^top
+    const int base = top - 32 * W;        // bit 0 of the window
+    uint32_t X[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) X[i] = 0;
+    bool sticky = false;
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        uint64_t mant;
+        int e;
+        bool ng;
+        if (!decompose(x[c], mant, e, ng)) continue;
+        int s = e - 53 - base;
+        if (s < 0) {
+            if (s <= -64) { sticky = true; continue; }
+            if (mant & ((1ull << (-s)) - 1)) sticky = true;
+            mant >>= -s;
+            s = 0;
+        }
+        add_shifted<W>(X, mant, s, ng);
+    }
+    int neg = 0;
+    if (is_negative<W>(X)) {
+        negate<W>(X);
+        neg = 1;
+        // a dropped positive remainder of a negative sum rounds the magnitude up
+    }
+    return mpf_round<L, W>(X, top, neg, sticky);
+}
+
+// successive round-to-nearest-even into N binary64 components
+template <int L, int N>
+__device__ __forceinline__ void mpf_to_exp(const MPF<L>& a, double* out) {
+    uint32_t mag[L];
+#pragma unroll
+    for (int i = 0; i < L; ++i) mag[i] = a.m[i];
+    bool neg = a.neg != 0;
+    const int E = a.e - 32 * L;
+#pragma unroll
+    for (int c = 0; c < N; ++c) {
+        const int Lb = bit_length<L>(mag);
+        double x = 0.0;
+        if (Lb > 0) {
+            if (Lb <= 53) {
+                const uint64_t q = (uint64_t)field32<L>(mag, 0) | ((uint64_t)field32<L>(mag, 32) << 32);
+                x = scalbn((double)(q & ((1ull << 53) - 1)), E);
+#pragma unroll
+                for (int i = 0; i < L; ++i) mag[i] = 0;
+                if (neg) x = -x;
+            } else {
+                const int sh = Lb - 53;
+                uint64_t q = ((uint64_t)field32<L>(mag, sh) | ((uint64_t)field32<L>(mag, sh + 32) << 32)) &
+                             ((1ull << 53) - 1);
+                const bool rb = bit_at<L>(mag, sh - 1) != 0;
+                const bool st = any_below<L>(mag, sh - 1);
+                mask_below<L>(mag, sh);
+                if (rb && (st || (q & 1))) {
+                    q += 1;
+                    complement_below<L>(mag, sh);
+                    x = scalbn((double)q, E + sh);
+                    if (neg) x = -x;
+                    neg = !neg;
+                } else {
+                    x = scalbn((double)q, E + sh);
+                    if (neg) x = -x;
+                }
+            }
+        }
+        out[c] = x;
+    }
+}
+
+template <int L>
+__device__ __forceinline__ MPF<L> mpf_neg(MPF<L> a) {
+    a.neg ^= 1;
+    return a;
+}
+
+// |a| vs |b|
+template <int L>
+__device__ __forceinline__ int mpf_abs_cmp(const MPF<L>& a, const MPF<L>& b) {
+    const bool za = mpf_zero<L>(a), zb = mpf_zero<L>(b);
+    if (za || zb) return za && zb ? 0 : (za ? -1 : 1);
+    if (a.e != b.e) return a.e > b.e ? 1 : -1;
+#pragma unroll
+    for (int i = L - 1; i >= 0; --i)
+        if (a.m[i] != b.m[i]) return a.m[i] > b.m[i] ? 1 : -1;
+    return 0;
+}
+
+// a * b, rounded to L words
+template <int L>
+__device__ __forceinline__ MPF<L> mpf_mul(const MPF<L>& a, const MPF<L>& b) {
+    if (mpf_zero<L>(a) || mpf_zero<L>(b)) return mpf_make_zero<L>();
+    uint32_t P[2 * L];
+#pragma unroll
+    for (int i = 0; i < 2 * L; ++i) P[i] = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        uint64_t c = 0;
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            const uint64_t t = (uint64_t)a.m[i] * b.m[j] + P[i + j] + c;
+            P[i + j] = (uint32_t)t;
+            c = t >> 32;
+        }
+        P[i + L] = (uint32_t)c;
+    }
+    // value = P * 2^(a.e + b.e - 64 L) = P * 2^((a.e + b.e) - 32 * 2L)
+    return mpf_round<L, 2 * L>(P, a.e + b.e, a.neg ^ b.neg, false);
+}
+
+// a + b, rounded to L words (guard words and a sticky keep it correctly rounded)
+template <int L>
+__device__ __forceinline__ MPF<L> mpf_add(const MPF<L>& a, const MPF<L>& b) {
+    if (mpf_zero<L>(b)) return a;
+    if (mpf_zero<L>(a)) return b;
+    const bool swap = mpf_abs_cmp<L>(a, b) < 0;
+    const MPF<L>& x = swap ? b : a;  // |x| >= |y|
+    const MPF<L>& y = swap ? a : b;
+    constexpr int W = L + 2;
+    uint32_t X[W], Y[W];
+    X[0] = 0;
+    X[1] = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i) X[i + 2] = x.m[i];
+    // y shifted right by d = x.e - y.e bits into the same window
+    const int d = x.e - y.e;
+    bool sticky = false;
+#pragma unroll
+    for (int i = 0; i < W; ++i) Y[i] = 0;
+    if (d < 32 * W) {
+        const int q = d >> 5, r = d & 31;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            // Y[i] = bits of (y.m << 64) >> d at word i
+            uint32_t lo = 0, hi = 0;
+#pragma unroll
+            for (int k = 0; k < L; ++k) {
+                if (k + 2 == i + q) lo = y.m[k];
+                if (k + 2 == i + q + 1) hi = y.m[k];
+            }
+            Y[i] = r ? (lo >> r) | (hi << (32 - r)) : lo;
+        }
+        // sticky: bits of y shifted out below the window
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            const int lowbit = 32 * (k + 2) - d;  // position of y.m[k] bit 0 in the window
+            if (lowbit < 0) {
+                const int keep_from = -lowbit;  // bits of y.m[k] below this are lost
+                if (keep_from >= 32) sticky |= y.m[k] != 0;
+                else sticky |= (y.m[k] & ((1u << keep_from) - 1u)) != 0;
+            }
+        }
+    } else {
+        sticky = true;
+    }
+    if (x.neg == y.neg) {
+        uint64_t c = 0;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const uint64_t s = (uint64_t)X[i] + Y[i] + c;
+            X[i] = (uint32_t)s;
+            c = s >> 32;
+        }
+        // carry out of the window: shift right one bit, keep the lost bit
+        if (c) {
+            sticky |= (X[0] & 1u) != 0;
+#pragma unroll
+            for (int i = 0; i < W - 1; ++i) X[i] = (X[i] >> 1) | (X[i + 1] << 31);
+            X[W - 1] = (X[W - 1] >> 1) | 0x80000000u;
+            return mpf_round<L, W>(X, x.e + 1, x.neg, sticky);
+        }
+        return mpf_round<L, W>(X, x.e, x.neg, sticky);
+    }
+    // |x| >= |y|: the exact difference is X - Y - delta with 0 <= delta < 1
+    // unit of the window (the bits of y below it); X - Y - 1 plus a set sticky
+    // stands for it whenever delta > 0
+    uint64_t brw = sticky ? 1u : 0u;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const uint64_t s = (uint64_t)X[i] - Y[i] - brw;
+        X[i] = (uint32_t)s;
+        brw = (s >> 63) & 1u;
+    }
+    return mpf_round<L, W>(X, x.e, x.neg, sticky);
+}
+
+template <int L>
+__device__ __forceinline__ MPF<L> mpf_sub(const MPF<L>& a, const MPF<L>& b) {
+    return mpf_add<L>(a, mpf_neg<L>(b));
+}
+
+// c - a b (two roundings)
+template <int L>
+__device__ __forceinline__ MPF<L> mpf_fms(const MPF<L>& c, const MPF<L>& a, const MPF<L>& b) {
+    return mpf_sub<L>(c, mpf_mul<L>(a, b));
+}
+
+template <int L>
+__device__ __forceinline__ MPF<L> mpf_from_double(double v) {
+    return mpf_from_exp<L, 1>(&v);
+}
+
+// 1 / b by Newton's iteration r <- r (2 - b r) from a binary64 start
+template <int L>
+__device__ __forceinline__ MPF<L> mpf_recip(const MPF<L>& b) {
+    // binary64 approximation of b
+    double bd[1];
+    {
+        const uint64_t top = ((uint64_t)b.m[L - 1] << 32) | b.m[L - 2];
+        double v = scalbn((double)(top >> 11), b.e - 53);
+        bd[0] = b.neg ? -v : v;
+    }
+    MPF<L> r = mpf_from_double<L>(1.0 / bd[0]);
+    const MPF<L> two = mpf_from_double<L>(2.0);
+    // 53 -> 106 -> 212 -> 424 bits
+    for (int it = 0; it < 4 && (53 << it) < 32 * L + 53; ++it) r = mpf_mul<L>(r, mpf_sub<L>(two, mpf_mul<L>(b, r)));
+    return r;
+}
+
+}  // namespace ozlu

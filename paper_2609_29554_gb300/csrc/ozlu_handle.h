@@ -40,6 +40,8 @@ struct ozlu_handle {
     bool timing = false;
     ozlu_stats stats = {};
     void* lu_scratch = nullptr;  // pivot-search scratch of ozlu_getrf
+    void* coop_scratch = nullptr;  // grid-barrier and candidate slots of the panel kernel
+    size_t coop_bytes = 0;
     // phase timing: (phase, start, end) event triples resolved in ozlu_get_stats
     std::vector<cudaEvent_t> pool;
     size_t pool_used = 0;
