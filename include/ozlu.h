@@ -56,7 +56,8 @@ enum {
     OZLU_BE_AUTO = 0, /* measured choice per shape (autotuner)                        */
     OZLU_BE_INT8 = 1, /* centered residues in int8, exact int32 accumulation          */
     OZLU_BE_FP8 = 2,  /* balanced base-17 digits in E4M3, Eq. (15), fp32 accumulation */
-    OZLU_BE_FP64 = 3  /* residues of ~23-bit primes in binary64, Eq. (17)             */
+    OZLU_BE_FP64 = 3, /* residues of ~23-bit primes in binary64, Eq. (17)             */
+    OZLU_BE_FP16 = 4  /* centered residues in binary16, fp32 accumulation, Eq. (14)   */
 };
 
 /* Options; an all-zero struct (or NULL) selects the defaults. */
@@ -130,6 +131,10 @@ int ozlu_getrs(ozlu_handle* handle, int nc, int p, int n, int nrhs,
  *   3 residues of A  int8 [l][t][i][h], h < k, planes (l, t) in order
  *   4 residues of B  int8 [l][t][j][h]
  *   5 t values      uint8 [gi][l][j][i] (column-major m x n per plane)
+ *   6 device error word (int32): 0, or OZLU_ERR_TIMEOUT when a bounded
+ *     wait inside a tensor-core GEMM gave up (sticky until the workspace
+ *     is reallocated)
+ * Residues (3, 4) are available for the INT8 back-end only.
  * bytes must be at least the size of the requested array.
  */
 int ozlu_debug_fetch(ozlu_handle* handle, int what, void* dst, size_t bytes);

@@ -15,6 +15,8 @@ Paper passages followed:
   * Sec. 3.2, "Truncation under cancellation": extra retained digit groups.
   * Sec. 4.2.6, Eq. (17): binary64 residues need K (m/2)^2 < 2^53.
   * Sec. 4.2.3, Eq. (15): FP8 balanced base-17 digits keep the INT8 set.
+  * Sec. 4.2.3, Eq. (14): binary16 residues (|r| <= 127) with an fp32
+    accumulator need K_pad S 127^2 < 2^24; the INT8 modulus set is kept.
 
 Readings where the paper is silent or garbled (each listed in the design doc):
   * the modulus order is descending (largest first); ascending order does not
@@ -122,6 +124,9 @@ def _accumulator_ok(backend: str, K: int, S: int) -> bool:
     if backend == "fp8":
         # Karatsuba planes of base-17 digits: |d0|,|d1|,|d0+d1| <= 15, FP32 sum
         return k_pad(K) * S * 15 * 15 < (1 << 24)
+    if backend == "fp16":
+        # Eq. (14): K_pad S 127^2 < 2^24 for binary16 residues, fp32 accumulator
+        return k_pad(K) * S * 127 * 127 < (1 << 24)
     if backend == "fp64":
         return True  # folded into the modulus bound of fp64_moduli
     raise ValueError(backend)

@@ -81,44 +81,63 @@ int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, c
         }
         return OZLU_OK;
     }
+    ozlu_opts o;
+    memset(&o, 0, sizeof o);
+    if (opts) o = *opts;
+    if (o.backend == OZLU_BE_AUTO) o.backend = OZLU_BE_INT8;
     const Plan* pl;
     const DevTable* tab;
-    int rc = plan_for(h, p, k, opts, &pl, &tab);
+    int rc = plan_for(h, p, k, &o, &pl, &tab);
     if (rc) return rc;
-    if (pl->backend != OZLU_BE_INT8) return OZLU_ERR_UNSUPPORTED;
+    const int be = pl->backend;
+    if (be == OZLU_BE_FP64) return OZLU_ERR_UNSUPPORTED;
+    const int mode = be == OZLU_BE_INT8 ? 0 : (be == OZLU_BE_FP8 ? 1 : 2);
+    const int P = mode == 1 ? 3 : 1, esz = mode == 2 ? 2 : 1;
     const int Mpad = (m + 127) / 128 * 128, Npad = (n + 127) / 128 * 128;
     const int Kpad = pl->Kpad;
     GemmLayout& L = h->last;
     L.m = m; L.n = n; L.k = k; L.Mpad = Mpad; L.Npad = Npad; L.Kpad = Kpad;
-    L.N = pl->N; L.S = pl->S; L.G = pl->G;
+    L.N = pl->N; L.S = pl->S; L.G = pl->G; L.backend = be;
     size_t off = 0;
     L.mu = off; off = align_up(off + sizeof(int) * m);
     L.nu = off; off = align_up(off + sizeof(int) * n);
-    L.ra = off; off = align_up(off + (size_t)pl->N * pl->S * Mpad * Kpad);
-    L.rb = off; off = align_up(off + (size_t)pl->N * pl->S * Npad * Kpad);
+    L.ra = off; off = align_up(off + (size_t)pl->N * pl->S * P * Mpad * Kpad * esz);
+    L.rb = off; off = align_up(off + (size_t)pl->N * pl->S * P * Npad * Kpad * esz);
     L.t = off;  off = align_up(off + (size_t)pl->G * pl->N * m * n);
+    L.err = off; off = align_up(off + sizeof(int));
+    const bool fresh = h->ws.cap < off;
     rc = h->ws.ensure(off);
     if (rc) return rc;
     char* base = (char*)h->ws.base;
     int* mu = (int*)(base + L.mu);
     int* nu = (int*)(base + L.nu);
-    int8_t* RA = (int8_t*)(base + L.ra);
-    int8_t* RB = (int8_t*)(base + L.rb);
+    void* RA = base + L.ra;
+    void* RB = base + L.rb;
     uint8_t* T = (uint8_t*)(base + L.t);
+    int* derr = (int*)(base + L.err);
+    if (fresh || h->err_off != L.err) {
+        if (cudaMemsetAsync(derr, 0, sizeof(int), s)) return OZLU_ERR_CUDA;
+        h->err_off = L.err;
+    }
     const int prev = h->open_phase;
     h->phase(PH_CONVERT);
     launch_row_shifts(A, lda, nc, m, k, pl->Q, mu, s);
     launch_col_shifts(B, ldb, nc, k, n, pl->Q, nu, s);
-    launch_convert(A, lda, nc, m, k, false, mu, *tab, Kpad, Mpad, RA, s);
-    launch_convert(B, ldb, nc, k, n, true, nu, *tab, Kpad, Npad, RB, s);
+    launch_convert(A, lda, nc, m, k, false, mu, *tab, Kpad, Mpad, RA, mode, s);
+    launch_convert(B, ldb, nc, k, n, true, nu, *tab, Kpad, Npad, RB, mode, s);
     h->phase(PH_GEMM);
-    launch_gemm_imma(RA, RB, m, n, Mpad, Npad, Kpad, *tab, T, s);
+    if (mode == 0) {
+        launch_gemm_imma((const int8_t*)RA, (const int8_t*)RB, m, n, Mpad, Npad, Kpad, *tab, T, s);
+    } else {
+        rc = launch_gemm_tc05(mode == 1, RA, RB, m, n, Mpad, Npad, Kpad, *tab, T, derr, s);
+        if (rc) return rc;
+    }
     h->phase(PH_CRT);
     launch_crt(T, m, n, mu, nu, *tab, nc, alpha, beta, C, ldc, s);
     h->phase(prev);
     h->stats.gemm_launches += 1;
     h->stats.crt_launches += 1;
-    h->stats.gemm_ops += 2.0 * m * n * (double)k * pl->N * pl->pair_terms;
+    h->stats.gemm_ops += 2.0 * m * n * (double)k * pl->N * pl->pair_terms * P;
     h->stats.crt_bytes += (double)pl->G * pl->N * m * n + 8.0 * nc * m * n * (beta ? 2 : 1);
     h->stats.convert_bytes += 8.0 * nc * ((double)m * k + (double)k * n) +
                               (double)pl->N * pl->S * ((double)Mpad + Npad) * Kpad;
@@ -281,6 +300,11 @@ int ozlu_debug_fetch(ozlu_handle* h, int what, void* dst, size_t bytes) {
         if (bytes < need) return -4;
         return cuda_rc(cudaMemcpy(dst, base + (what == 1 ? L.mu : L.nu), need, cudaMemcpyDeviceToHost));
     }
+    if (what == 6) {
+        if (bytes < sizeof(int)) return -4;
+        return cuda_rc(cudaMemcpy(dst, base + L.err, sizeof(int), cudaMemcpyDeviceToHost));
+    }
+    if ((what == 3 || what == 4) && L.backend != OZLU_BE_INT8) return OZLU_ERR_UNSUPPORTED;
     if (what == 3 || what == 4) {
         const int R = what == 3 ? L.m : L.n, Rpad = what == 3 ? L.Mpad : L.Npad;
         const size_t need = (size_t)L.N * L.S * R * L.k;

@@ -1,5 +1,7 @@
 // (S1) shared exponents and (S2)+(S3) fused conversion of expansions to
 // centered residue planes (Sec. 3.1, Sec. 3.2 Eq. (2), Sec. 3.3 Eq. (12)).
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <limits.h>
 
 #include "mp_device.cuh"
@@ -67,10 +69,30 @@ __device__ __forceinline__ int centered_residue(const uint32_t (&mag)[MAXD], boo
 //   A side (is_b = 0): element (r, h) of an R x K matrix, plane [l][t][r][h]
 //   B side (is_b = 1): element (h, r) of a K x R matrix, plane [l][t][r][h]
 // Threads cover the padded range [0, Rpad) x [0, Kpad) and write zeros there.
+// store residue r of plane (l, t) at element offset off, in the back-end's encoding
+template <int MODE>
+__device__ __forceinline__ void put_residue(void* planes, size_t plane, int l, int S, int t,
+                                            size_t off, int r) {
+    if (MODE == 0) {
+        ((int8_t*)planes)[(size_t)(l * S + t) * plane + off] = (int8_t)r;
+    } else if (MODE == 1) {
+        // Eq. (15): r = 17 d1 + d0, d1 = round(r / 17) (no ties: 17 is odd)
+        const int d1 = (2 * r + 17 + 238) / 34 - 7;
+        const int d0 = r - 17 * d1;
+        uint8_t* p8 = (uint8_t*)planes + (size_t)((l * S + t) * 3) * plane + off;
+        p8[0] = (uint8_t)__nv_cvt_float_to_fp8((float)d0, __NV_SATFINITE, __NV_E4M3);
+        p8[plane] = (uint8_t)__nv_cvt_float_to_fp8((float)d1, __NV_SATFINITE, __NV_E4M3);
+        p8[2 * plane] = (uint8_t)__nv_cvt_float_to_fp8((float)(d0 + d1), __NV_SATFINITE, __NV_E4M3);
+    } else {
+        ((__half*)planes)[(size_t)(l * S + t) * plane + off] = __int2half_rn(r);
+    }
+}
+
+template <int MODE>
 __global__ void __launch_bounds__(256) convert_kernel(
     const double* __restrict__ X, long long ld, int nc, int R, int K, int is_b,
     const int* __restrict__ shifts, const __grid_constant__ DevTable tab, int Kpad, int Rpad,
-    int8_t* __restrict__ planes) {
+    void* __restrict__ planes) {
     const int h = blockIdx.x * 32 + (threadIdx.x & 31);
     const int r = blockIdx.y * 8 + (threadIdx.x >> 5);
     if (h >= Kpad || r >= Rpad) return;
@@ -78,7 +100,7 @@ __global__ void __launch_bounds__(256) convert_kernel(
     const size_t off = (size_t)r * Kpad + h;
     if (r >= R || h >= K) {
         for (int l = 0; l < tab.N; ++l)
-            for (int t = 0; t < tab.S; ++t) planes[(size_t)(l * tab.S + t) * plane + off] = 0;
+            for (int t = 0; t < tab.S; ++t) put_residue<MODE>(planes, plane, l, tab.S, t, off, 0);
         return;
     }
     const double* x = is_b ? X + ((long long)h + (long long)r * ld) * nc
@@ -139,7 +161,7 @@ __global__ void __launch_bounds__(256) convert_kernel(
         }
         for (int l = 0; l < tab.N; ++l) {
             const int res = centered_residue(D, neg, tab.H, tab, l);
-            planes[(size_t)(l * S + t) * plane + off] = (int8_t)res;
+            put_residue<MODE>(planes, plane, l, S, t, off, res);
         }
     }
 }
@@ -161,14 +183,18 @@ void launch_col_shifts(const double* B, long long ldb, int nc, int k, int n, int
 }
 
 void launch_convert(const double* X, long long ld, int nc, int rows, int cols, bool is_b,
-                    const int* shifts, const DevTable& tab, int Kpad, int Rpad, int8_t* planes,
-                    cudaStream_t s) {
+                    const int* shifts, const DevTable& tab, int Kpad, int Rpad, void* planes,
+                    int mode, cudaStream_t s) {
     // A side: rows = R, cols = K; B side: rows = K, cols = R
     const int R = is_b ? cols : rows;
     const int K = is_b ? rows : cols;
     dim3 grid((Kpad + 31) / 32, (Rpad + 7) / 8);
-    convert_kernel<<<grid, 256, 0, s>>>(X, ld, nc, R, K, is_b ? 1 : 0, shifts, tab, Kpad, Rpad,
-                                        planes);
+    if (mode == 0)
+        convert_kernel<0><<<grid, 256, 0, s>>>(X, ld, nc, R, K, is_b ? 1 : 0, shifts, tab, Kpad, Rpad, planes);
+    else if (mode == 1)
+        convert_kernel<1><<<grid, 256, 0, s>>>(X, ld, nc, R, K, is_b ? 1 : 0, shifts, tab, Kpad, Rpad, planes);
+    else
+        convert_kernel<2><<<grid, 256, 0, s>>>(X, ld, nc, R, K, is_b ? 1 : 0, shifts, tab, Kpad, Rpad, planes);
 }
 
 }  // namespace ozlu

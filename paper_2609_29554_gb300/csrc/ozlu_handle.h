@@ -24,8 +24,8 @@ struct PlanEntry {
 
 // byte offsets of the last ozlu_gemm's intermediates inside the workspace
 struct GemmLayout {
-    int m = 0, n = 0, k = 0, Mpad = 0, Npad = 0, Kpad = 0, N = 0, S = 0, G = 0;
-    size_t mu = 0, nu = 0, ra = 0, rb = 0, t = 0;
+    int m = 0, n = 0, k = 0, Mpad = 0, Npad = 0, Kpad = 0, N = 0, S = 0, G = 0, backend = 0;
+    size_t mu = 0, nu = 0, ra = 0, rb = 0, t = 0, err = 0;
 };
 
 }  // namespace ozlu
@@ -37,6 +37,7 @@ struct ozlu_handle {
     ozlu::Workspace stage;  // host-argument staging
     std::map<std::tuple<int, int, int, int, int, int>, ozlu::PlanEntry> plans;
     ozlu::GemmLayout last;
+    size_t err_off = (size_t)-1;  // workspace offset of the device error word
     bool timing = false;
     ozlu_stats stats = {};
     void* lu_scratch = nullptr;  // pivot-search scratch of ozlu_getrf

@@ -54,9 +54,14 @@ void launch_col_shifts(const double* B, long long ldb, int nc, int k, int n, int
                        int* nu, cudaStream_t s);
 // (S2)+(S3) fused: expansions -> Q-bit integers -> S digits -> residue planes.
 // A side: planes [l][t][Mpad][Kpad] (row i, K contiguous); B side: [l][t][Npad][Kpad].
+// mode 0: int8 residues (1 plane); 1: E4M3 base-17 digits d0, d1, d0+d1 (3 planes);
+// 2: binary16 residues (1 plane, 2-byte elements).  Plane index (l * S + t) * P + p.
 void launch_convert(const double* X, long long ld, int nc, int rows, int cols,
                     bool is_b, const int* shifts, const DevTable& tab, int Kpad,
-                    int Rpad, int8_t* planes, cudaStream_t s);
+                    int Rpad, void* planes, int mode, cudaStream_t s);
+// (S4) on tcgen05: FP8 base-17 Karatsuba (fp8 = true) or FP16 residues
+int launch_gemm_tc05(bool fp8, const void* RA, const void* RB, int m, int n, int Mpad, int Npad,
+                     int Kpad, const DevTable& tab, uint8_t* T, int* err, cudaStream_t s);
 // (S4)+(S5 t_l) INT8 residue GEMMs with the modular epilogue; T[gi][l][j][i].
 void launch_gemm_imma(const int8_t* RA, const int8_t* RB, int m, int n, int Mpad,
                       int Npad, int Kpad, const DevTable& tab, uint8_t* T,

@@ -96,7 +96,7 @@ int make_plan(int p, int K, const ozlu_opts* o, Plan& out) {
     if (!o) o = &d;
     const int be = o->backend == OZLU_BE_AUTO ? OZLU_BE_INT8 : o->backend;
     if (p < 1 || K < 1) return OZLU_ERR_CAPACITY;
-    if (be != OZLU_BE_INT8 && be != OZLU_BE_FP8 && be != OZLU_BE_FP64) return -1;
+    if (be != OZLU_BE_INT8 && be != OZLU_BE_FP8 && be != OZLU_BE_FP64 && be != OZLU_BE_FP16) return -1;
     const int slack = ceil_log2(2.0 * K) + 16 + o->g_ex;
     const int Kpad = (K + 127) / 128 * 128;
     std::vector<int> mods = be == OZLU_BE_FP64 ? fp64_set(K, MAXMOD) : int8_set();
@@ -107,6 +107,8 @@ int make_plan(int p, int K, const ozlu_opts* o, Plan& out) {
         // Karatsuba planes (|digit sums| <= 15)
         if (be == OZLU_BE_INT8 && (double)Kpad * S * 127.0 * 127.0 >= ldexp(1.0, 31)) continue;
         if (be == OZLU_BE_FP8 && (double)Kpad * S * 225.0 >= ldexp(1.0, 24)) continue;
+        // Eq. (14): binary16 residues with an fp32 accumulator
+        if (be == OZLU_BE_FP16 && (double)Kpad * S * 127.0 * 127.0 >= ldexp(1.0, 24)) continue;
         const int w = (p + slack + S - 1) / S;
         const double need = 2.0 * w + log2((double)K) + log2((double)S) + 5.0;
         double cum = 0.0;

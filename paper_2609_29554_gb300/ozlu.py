@@ -25,7 +25,7 @@ OZLU_ERR_NOMEM = 1002
 OZLU_ERR_CAPACITY = 1003
 OZLU_ERR_TIMEOUT = 1004
 OZLU_ERR_UNSUPPORTED = 1005
-BACKENDS = {"auto": 0, "int8": 1, "fp8": 2, "fp64": 3}
+BACKENDS = {"auto": 0, "int8": 1, "fp8": 2, "fp64": 3, "fp16": 4}
 
 _lib = None
 
