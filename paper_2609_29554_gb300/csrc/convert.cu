@@ -13,16 +13,26 @@ namespace {
 constexpr int NO_EXP = INT_MIN;
 
 // mu_i = (Q-1) - max_h frexp_exp(a_ih[0]); 0 for an all-zero row.
-__global__ void row_shift_kernel(const double* __restrict__ A, long long lda, int nc, int m,
-                                 int k, int Q, int* __restrict__ mu) {
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= m) return;
+// Block of 32 rows x 8 lanes along h (consecutive rows are adjacent in memory).
+__global__ void __launch_bounds__(256) row_shift_kernel(const double* __restrict__ A, long long lda,
+                                                        int nc, int m, int k, int Q,
+                                                        int* __restrict__ mu) {
+    __shared__ int red[8][32];
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int i = blockIdx.x * 32 + tx;
     int E = NO_EXP;
-    for (int h = 0; h < k; ++h) {
-        const double x = A[((long long)i + (long long)h * lda) * nc];
-        if (x != 0.0) E = max(E, frexp_exp(x));
+    if (i < m)
+        for (int h = ty; h < k; h += 8) {
+            const double x = A[((long long)i + (long long)h * lda) * nc];
+            if (x != 0.0) E = max(E, frexp_exp(x));
+        }
+    red[ty][tx] = E;
+    __syncthreads();
+    if (ty == 0 && i < m) {
+#pragma unroll
+        for (int r = 1; r < 8; ++r) E = max(E, red[r][tx]);
+        mu[i] = E == NO_EXP ? 0 : (Q - 1) - E;
     }
-    mu[i] = E == NO_EXP ? 0 : (Q - 1) - E;
 }
 
 // nu_j over column j of B (k x n): one warp per column.
@@ -44,18 +54,18 @@ __global__ void col_shift_kernel(const double* __restrict__ B, long long ldb, in
 
 constexpr int MAXD = 9;  // words of one balanced digit (w + 2 bits)
 
-// Residue of sign * mag (mag < 2^(32 MAXD)) modulo m, centered (S3):
-// r in [-floor(m/2), ceil(m/2) - 1].
-__device__ __forceinline__ int centered_residue(const uint32_t (&mag)[MAXD], bool neg, int H,
+// Residue of sign * mag (mag < 2^(16 H)) modulo m, centered (S3):
+// r in [-floor(m/2), ceil(m/2) - 1].  H (16-bit halves) is a template
+// parameter so the sum unrolls exactly.
+template <int H>
+__device__ __forceinline__ int centered_residue(const uint32_t (&mag)[MAXD], bool neg,
                                                 const DevTable& tab, int l) {
     const uint32_t m = (uint32_t)tab.mod[l];
     uint32_t acc = 0;
 #pragma unroll
-    for (int j = 0; j < 2 * MAXD; ++j) {
-        if (j < H) {
-            const uint32_t half = (mag[j >> 1] >> (16 * (j & 1))) & 0xffffu;
-            acc += half * tab.pow16[l][j];
-        }
+    for (int j = 0; j < H; ++j) {
+        const uint32_t half = (mag[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+        acc += half * tab.pow16[l][j];
     }
     uint32_t r = mod_small(acc, m, tab.magic[l]);
     if (neg && r) r = m - r;
@@ -88,7 +98,7 @@ __device__ __forceinline__ void put_residue(void* planes, size_t plane, int l, i
     }
 }
 
-template <int MODE>
+template <int MODE, int H>
 __global__ void __launch_bounds__(256) convert_kernel(
     const double* __restrict__ X, long long ld, int nc, int R, int K, int is_b,
     const int* __restrict__ shifts, const __grid_constant__ DevTable tab, int Kpad, int Rpad,
@@ -160,7 +170,7 @@ __global__ void __launch_bounds__(256) convert_kernel(
             for (int k2 = 0; k2 < MAXD; ++k2) D[k2] = T[k2];
         }
         for (int l = 0; l < tab.N; ++l) {
-            const int res = centered_residue(D, neg, tab.H, tab, l);
+            const int res = centered_residue<H>(D, neg, tab, l);
             put_residue<MODE>(planes, plane, l, S, t, off, res);
         }
     }
@@ -171,7 +181,7 @@ __global__ void __launch_bounds__(256) convert_kernel(
 void launch_row_shifts(const double* A, long long lda, int nc, int m, int k, int Q, int* mu,
                        cudaStream_t s) {
     if (m <= 0) return;
-    row_shift_kernel<<<(m + 127) / 128, 128, 0, s>>>(A, lda, nc, m, k, Q, mu);
+    row_shift_kernel<<<(m + 31) / 32, 256, 0, s>>>(A, lda, nc, m, k, Q, mu);
 }
 
 void launch_col_shifts(const double* B, long long ldb, int nc, int k, int n, int Q, int* nu,
@@ -189,12 +199,23 @@ void launch_convert(const double* X, long long ld, int nc, int rows, int cols, b
     const int R = is_b ? cols : rows;
     const int K = is_b ? rows : cols;
     dim3 grid((Kpad + 31) / 32, (Rpad + 7) / 8);
-    if (mode == 0)
-        convert_kernel<0><<<grid, 256, 0, s>>>(X, ld, nc, R, K, is_b ? 1 : 0, shifts, tab, Kpad, Rpad, planes);
-    else if (mode == 1)
-        convert_kernel<1><<<grid, 256, 0, s>>>(X, ld, nc, R, K, is_b ? 1 : 0, shifts, tab, Kpad, Rpad, planes);
-    else
-        convert_kernel<2><<<grid, 256, 0, s>>>(X, ld, nc, R, K, is_b ? 1 : 0, shifts, tab, Kpad, Rpad, planes);
+    switch (mode * 32 + tab.H) {
+#define OZLU_CONV(M, HH) \
+    case M * 32 + HH: \
+        convert_kernel<M, HH><<<grid, 256, 0, s>>>(X, ld, nc, R, K, is_b ? 1 : 0, shifts, tab, Kpad, Rpad, planes); \
+        break;
+#define OZLU_CONV_M(M) OZLU_CONV(M, 2) OZLU_CONV(M, 3) OZLU_CONV(M, 4) OZLU_CONV(M, 5) OZLU_CONV(M, 6) \
+    OZLU_CONV(M, 7) OZLU_CONV(M, 8) OZLU_CONV(M, 9) OZLU_CONV(M, 10) OZLU_CONV(M, 11) OZLU_CONV(M, 12) \
+    OZLU_CONV(M, 13) OZLU_CONV(M, 14) OZLU_CONV(M, 15) OZLU_CONV(M, 16)
+        OZLU_CONV_M(0)
+        OZLU_CONV_M(1)
+        OZLU_CONV_M(2)
+#undef OZLU_CONV_M
+#undef OZLU_CONV
+        default:
+            convert_kernel<0, 16><<<grid, 256, 0, s>>>(X, ld, nc, R, K, is_b ? 1 : 0, shifts, tab, Kpad, Rpad,
+                                                      planes);
+    }
 }
 
 }  // namespace ozlu

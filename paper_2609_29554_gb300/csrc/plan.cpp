@@ -164,10 +164,11 @@ void fill_table(const Plan& pl, DevTable& t) {
             t.pow16[l][j] = (uint32_t)r;
             r = (r << 16) % m;
         }
-        for (int wd = 0; wd < pl.WG; ++wd)
+        // all MAXWG low words: a kernel may work modulo 2^(32 W) for any W >= WG
+        for (int wd = 0; wd < MAXWG; ++wd)
             t.Mlow[l][wd] = wd < (int)pl.M[l].size() ? pl.M[l][wd] : 0u;
     }
-    for (int wd = 0; wd < pl.WG; ++wd) t.Plow[wd] = wd < (int)pl.P.size() ? pl.P[wd] : 0u;
+    for (int wd = 0; wd < MAXWG; ++wd) t.Plow[wd] = wd < (int)pl.P.size() ? pl.P[wd] : 0u;
 }
 
 }  // namespace ozlu
