@@ -157,6 +157,33 @@ typedef struct {
 int ozlu_set_timing(ozlu_handle* handle, int enable);
 int ozlu_get_stats(ozlu_handle* handle, ozlu_stats* out);
 
+/*
+ * C = beta * C + alpha * A * B like ozlu_gemm with backend OZLU_BE_INT8, for
+ * callers that must not allocate (the paper has no counterpart: this is an
+ * interface of this library).  A host that has given nearly all device memory
+ * to its own pool allocator, or a latency-critical caller that cannot afford
+ * the synchronisation a cudaMalloc may imply, can call it: it takes no
+ * handle and allocates neither device nor host memory.
+ *   Arguments as ozlu_gemm (without handle and options), plus the stream
+ *   (cudaStream_t as void*, NULL = default stream); A, B, C must be device
+ *   pointers (a host pointer is rejected as an invalid argument), k >= 1.
+ *   Scratch: one fixed 16 MiB device array inside the library, held by every
+ *   GPU that loads it until the process exits.  Problems whose intermediates
+ *   do not fit (for QD, m = n = k = 256 fits; 384 does not) return
+ *   OZLU_ERR_CAPACITY.
+ *   The first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress, with that device current) and caches it; make that
+ *   first call before any stream capture.
+ *   All calls share the array: calls that overlap on the GPU (other streams,
+ *   other host threads) race and must be serialised by the caller.  Nothing
+ *   needs clearing between calls: every byte read is written first.
+ * Returns 0, -i for invalid argument i (nc = 1), or an OZLU_ERR_* code; the
+ * work is stream ordered (the call does not wait for it).
+ */
+int ozlu_gemm_noalloc(int nc, int p, int m, int n, int k, int alpha, const double* A,
+                      long long lda, const double* B, long long ldb, int beta, double* C,
+                      long long ldc, void* stream);
+
 /* Version string of the library. */
 const char* ozlu_version(void);
 

@@ -67,6 +67,7 @@ SIGNATURES = {
     "ozlu_debug_fetch": (_I, [_P, _I, _P, ctypes.c_size_t]),
     "ozlu_set_timing": (_I, [_P, _I]),
     "ozlu_get_stats": (_I, [_P, ctypes.POINTER(ozlu_stats)]),
+    "ozlu_gemm_noalloc": (_I, [_I, _I, _I, _I, _I, _I, _P, _L, _P, _L, _I, _P, _L, _P]),
 }
 
 
@@ -158,6 +159,13 @@ def ozlu_getrf(h, nc, p, n, A, lda, ipiv, nb, info, opts=None):
 def ozlu_getrs(h, nc, p, n, nrhs, LU, lda, ipiv, B, ldb, opts=None):
     _check("ozlu_getrs", lib().ozlu_getrs(h, nc, p, n, nrhs, _ptr(LU), lda, _ptr(ipiv), _ptr(B),
                                           ldb, ctypes.byref(opts) if opts else None))
+
+
+def ozlu_gemm_noalloc(nc, p, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, stream=None):
+    """The allocation-free GEMM (device tensors only; see include/ozlu.h)."""
+    _check("ozlu_gemm_noalloc", lib().ozlu_gemm_noalloc(nc, p, m, n, k, alpha, _ptr(A), lda, _ptr(B),
+                                                        ldb, beta, _ptr(C), ldc,
+                                                        _stream_ptr(stream)))
 
 
 def ozlu_debug_fetch(h, what, out: np.ndarray):
