@@ -30,6 +30,9 @@ constexpr int PIV_THREADS = 256;
 constexpr int PIV_BLOCKS = 152;
 constexpr int MAXPART = 1024;   // block partials of a column step
 constexpr int STEP_ROWS = 16;   // rows per block of a column step
+constexpr int LCT = 4;          // laswp: columns per block
+constexpr int LHASH = 2048;     // laswp: hash slots (>= 2 x affected rows)
+constexpr int LMAXB = 512;      // laswp: interchanges per call
 
 // limbs of the panel arithmetic: 32 L >= 53 nc + 22
 template <int N>
@@ -44,6 +47,10 @@ struct LuScratch {
     int info;
     double pval[MAXPART][4];    // block candidates (expansion values)
     int pidx[MAXPART];
+    int plist[1 + 4 * LMAXB];   // interchange permutation: count, (dst, src) pairs
+    // triangle of a base triangular solve as L-limb floats: [k][i], then the
+    // reciprocal diagonal (upper case)
+    unsigned char tri[(BASE * BASE + BASE) * sizeof(MPF<8>)];
 };
 
 template <int L>
@@ -319,12 +326,13 @@ __global__ void __launch_bounds__(128) column_step_kernel(double* A, long long l
 // The grid barrier spins with an iteration limit; on expiry the kernel records
 // OZLU_ERR_TIMEOUT in the scratch and returns.
 constexpr int COOP_MAXG = 304;           // blocks (up to 2 per SM)
-constexpr int COOP_THREADS = 128;
-constexpr long long BARRIER_SPIN_LIMIT = 20000000;  // ~2 s with 100 ns naps
+constexpr int COOP_THREADS = 256;
+constexpr long long BARRIER_SPIN_LIMIT = 40000000;  // about 2 s with 32 ns naps
 
 template <int L>
 struct CoopSlot {
     MPF<L> row[BASE];   // candidate row (all b columns)
+    MPF<L> rec;         // 1 / its entry in the pivot column (0 for a zero candidate)
     int idx;            // its global row index, -1 if none
 };
 
@@ -357,7 +365,7 @@ __device__ __forceinline__ bool grid_barrier(CoopScratch<L>* sc) {
                     atomicExch(&sc->error, OZLU_ERR_TIMEOUT);
                     break;
                 }
-                __nanosleep(100);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -387,6 +395,22 @@ __device__ __forceinline__ bool mpf_better(const MPF<L>& a, int ia, const MPF<L>
     return c > 0 || (c == 0 && ia < ib);
 }
 
+// warp-wide argmax of (|v|, first index): every lane ends with the winner
+template <int L>
+__device__ __forceinline__ void warp_best(MPF<L>& v, int& idx, int& aux) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        MPF<L> w;
+#pragma unroll
+        for (int q = 0; q < L; ++q) w.m[q] = __shfl_xor_sync(0xffffffffu, v.m[q], o);
+        w.e = __shfl_xor_sync(0xffffffffu, v.e, o);
+        w.neg = __shfl_xor_sync(0xffffffffu, v.neg, o);
+        const int wi = __shfl_xor_sync(0xffffffffu, idx, o);
+        const int wa = __shfl_xor_sync(0xffffffffu, aux, o);
+        if (mpf_better<L>(w, wi, v, idx)) { v = w; idx = wi; aux = wa; }
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
     double* A, long long lda, int n, int c0, int b, int p0, int p1, int rows_per_block,
@@ -396,9 +420,10 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
     MPF<L>* a = reinterpret_cast<MPF<L>*>(smraw);  // [r][k], r < rows_per_block, k < b
     __shared__ MPF<L> prow[BASE];
     __shared__ MPF<L> rec;
+    __shared__ MPF<L> crec;  // reciprocal of this block's next candidate
     __shared__ int s_piv, s_widx;
-    __shared__ MPF<L> cv[COOP_THREADS];
-    __shared__ int ci[COOP_THREADS];
+    __shared__ MPF<L> cv[1];
+    __shared__ int ci[1];
     const int g = blockIdx.x, G = gridDim.x, tid = threadIdx.x;
     const int r0 = c0 + g * rows_per_block;
     const int r1 = min(n, r0 + rows_per_block);
@@ -411,34 +436,40 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
     }
     __syncthreads();
 
-    // candidate of this block for local column kc among rows >= row_lo
-    auto publish = [&](int kc, int row_lo) {
+    // this block's best candidate (largest |a|, lowest row on ties) in local
+    // column kc among rows >= row_lo; result in cv[0], ci[0]
+    // (warp 0 only; the result is in cv[0], ci[0] after the caller's barrier)
+    auto candidate = [&](int kc, int row_lo) {
         MPF<L> best = mpf_make_zero<L>();
-        int bi = -1;
-        for (int r = tid; r < nr; r += COOP_THREADS) {
+        int bi = -1, aux = 0;
+        for (int r = tid; r < nr; r += 32) {
             const int i = r0 + r;
             if (i < row_lo) continue;
             if (mpf_better<L>(a[r * b + kc], i, best, bi)) { best = a[r * b + kc]; bi = i; }
         }
-        cv[tid] = best;
-        ci[tid] = bi;
-        __syncthreads();
-        for (int s = COOP_THREADS / 2; s > 0; s >>= 1) {
-            if (tid < s && mpf_better<L>(cv[tid + s], ci[tid + s], cv[tid], ci[tid])) {
-                cv[tid] = cv[tid + s];
-                ci[tid] = ci[tid + s];
-            }
-            __syncthreads();
+        warp_best<L>(best, bi, aux);
+        if (tid == 0) {
+            cv[0] = best;
+            ci[0] = bi;
         }
+    };
+    // publish the candidate row (after every column of it is final) and its reciprocal
+    auto publish = [&](int kc) {
         CoopSlot<L>& slot = sc->part[kc & 1][g];
         const int wi = ci[0];
-        if (tid == 0) slot.idx = wi;
+        if (tid == 0) {
+            slot.idx = wi;
+            slot.rec = crec;
+        }
         if (wi >= 0)
             for (int k = tid; k < b; k += COOP_THREADS) slot.row[k] = a[(wi - r0) * b + k];
         __syncthreads();
     };
 
-    publish(0, c0);
+    if (tid < 32) candidate(0, c0);
+    if (tid == 0) crec = (ci[0] >= 0 && !mpf_zero<L>(cv[0])) ? mpf_recip<L>(cv[0]) : mpf_make_zero<L>();
+    __syncthreads();
+    publish(0);
     for (int kc = 0; kc < b; ++kc) {
         const int c = c0 + kc;
         // the owner of row c leaves its old contents for the pivot row's owner
@@ -446,35 +477,24 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
             for (int k = tid; k < b; k += COOP_THREADS) sc->orow[kc & 1][k] = a[(c - r0) * b + k];
         if (!grid_barrier<L>(sc)) return;
         // every block reduces the same partials to the same pivot
-        {
+        if (tid < 32) {
             MPF<L> best = mpf_make_zero<L>();
             int bi = -1, bw = -1;
-            for (int q = tid; q < G; q += COOP_THREADS) {
+            for (int q = tid; q < G; q += 32) {
                 const CoopSlot<L>& slot = sc->part[kc & 1][q];
                 const int iv = __ldcg(&slot.idx);
                 if (iv < 0) continue;
                 const MPF<L> v = ld_cg<L>(&slot.row[kc]);
                 if (mpf_better<L>(v, iv, best, bi)) { best = v; bi = iv; bw = q; }
             }
-            cv[tid] = best;
-            ci[tid] = bi;
-            __shared__ int cw[COOP_THREADS];
-            cw[tid] = bw;
-            __syncthreads();
-            for (int s = COOP_THREADS / 2; s > 0; s >>= 1) {
-                if (tid < s && mpf_better<L>(cv[tid + s], ci[tid + s], cv[tid], ci[tid])) {
-                    cv[tid] = cv[tid + s];
-                    ci[tid] = ci[tid + s];
-                    cw[tid] = cw[tid + s];
-                }
-                __syncthreads();
-            }
+            warp_best<L>(best, bi, bw);
             if (tid == 0) {
-                s_piv = ci[0] < 0 ? c : ci[0];
-                s_widx = cw[0];
+                s_piv = bi < 0 ? c : bi;
+                s_widx = bw;
+                if (bw >= 0) rec = ld_cg<L>(&sc->part[kc & 1][bw].rec);
             }
-            __syncthreads();
         }
+        __syncthreads();
         const int piv = s_piv;
         // new row c = the pivot row
         for (int k = tid; k < b; k += COOP_THREADS)
@@ -502,23 +522,35 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
                 }
             }
         }
-        if (tid == 0 && !zero) rec = mpf_recip<L>(prow[kc]);
         __syncthreads();
+        const int lo = max(r0, c + 1) - r0;
+        const int rows = nr - lo;
+        const int cols = b - kc - 1;
         if (!zero) {
-            // multipliers and the rank-1 update of this block's rows below c
-            const int lo = max(r0, c + 1) - r0;
-            for (int r = lo + tid; r < nr; r += COOP_THREADS)
-                a[r * b + kc] = mpf_mul<L>(a[r * b + kc], rec);
-            __syncthreads();
-            const int cols = b - kc - 1;
-            const int rows = nr - lo;
-            for (int p = tid; p < rows * cols; p += COOP_THREADS) {
-                const int r = lo + p / cols, k = kc + 1 + (p - (p / cols) * cols);
+            // multipliers, then the next column first (its candidate is needed next)
+            for (int r = lo + tid; r < nr; r += COOP_THREADS) {
+                const MPF<L> l = mpf_mul<L>(a[r * b + kc], rec);
+                a[r * b + kc] = l;
+                if (cols > 0) a[r * b + kc + 1] = mpf_fms<L>(a[r * b + kc + 1], l, prow[kc + 1]);
+            }
+        }
+        __syncthreads();
+        if (cols == 0) break;
+        // lookahead: warp 0 picks the next candidate and forms its reciprocal
+        // while the other warps update the remaining columns
+        if (tid < 32) {
+            candidate(kc + 1, c + 1);
+            if (tid == 0) crec = (ci[0] >= 0 && !mpf_zero<L>(cv[0])) ? mpf_recip<L>(cv[0]) : mpf_make_zero<L>();
+        } else if (!zero && cols > 1) {
+            const int rest = cols - 1;
+            const int total = rows * rest;
+            for (int p = tid - 32; p < total; p += COOP_THREADS - 32) {
+                const int r = lo + p / rest, k = kc + 2 + (p - (p / rest) * rest);
                 a[r * b + k] = mpf_fms<L>(a[r * b + k], a[r * b + kc], prow[k]);
             }
         }
         __syncthreads();
-        if (kc + 1 < b) publish(kc + 1, c + 1);
+        publish(kc + 1);
     }
     for (int p = tid; p < nr * b; p += COOP_THREADS) {
         const int r = p / b, k = p - r * b;
@@ -543,31 +575,131 @@ __global__ void laswp_kernel(double* A, long long lda, int j0, int j1, int k0, i
     }
 }
 
+// Interchanges k in [k0, k1) (ipiv 1-based) applied to columns [j0, j1) as one
+// permutation: every block replays the swaps on the few affected rows (a
+// shared-memory hash map: position -> row whose contents end up there), then
+// gathers those rows of its LCT columns into shared memory and writes them
+// back permuted.  Replaces the column-serial swap chain.
+
+// one block: the (destination, source) row pairs of the interchanges
+__global__ void __launch_bounds__(256) laswp_list_kernel(int k0, int k1, const int* ipiv, int* list) {
+    __shared__ int hkey[LHASH], hval[LHASH];
+    __shared__ int cnt;
+    for (int i = threadIdx.x; i < LHASH; i += blockDim.x) hkey[i] = -1;
+    if (threadIdx.x == 0) cnt = 0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        auto slot = [&](int row) {
+            int h = (int)(((unsigned)row * 2654435761u) & (LHASH - 1));
+            while (hkey[h] != -1 && hkey[h] != row) h = (h + 1) & (LHASH - 1);
+            return h;
+        };
+        for (int k = k0; k < k1; ++k) {
+            const int p = ipiv[k] - 1;
+            if (p == k) continue;
+            const int sk = slot(k);
+            if (hkey[sk] == -1) { hkey[sk] = k; hval[sk] = k; }
+            const int sp = slot(p);
+            if (hkey[sp] == -1) { hkey[sp] = p; hval[sp] = p; }
+            const int t = hval[sk];
+            hval[sk] = hval[sp];
+            hval[sp] = t;
+        }
+    }
+    __syncthreads();
+    for (int h = threadIdx.x; h < LHASH; h += blockDim.x)
+        if (hkey[h] != -1 && hval[h] != hkey[h]) {
+            const int c = atomicAdd(&cnt, 1);
+            list[1 + 2 * c] = hkey[h];
+            list[2 + 2 * c] = hval[h];
+        }
+    __syncthreads();
+    if (threadIdx.x == 0) list[0] = cnt;
+}
+
+template <int N>
+__global__ void __launch_bounds__(256) laswp_apply_kernel(double* A, long long lda, int j0, int j1,
+                                                          const int* list) {
+    extern __shared__ __align__(16) double buf[];  // [entry][col][N]
+    const int ne = list[0];
+    const int jb = j0 + blockIdx.x * LCT;
+    for (int t = threadIdx.x; t < ne * LCT; t += blockDim.x) {
+        const int e = t / LCT, cc = t - e * LCT, j = jb + cc;
+        if (j < j1) {
+            const double* x = elem(A, lda, N, list[2 + 2 * e], j);
+#pragma unroll
+            for (int q = 0; q < N; ++q) buf[(e * LCT + cc) * N + q] = x[q];
+        }
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < ne * LCT; t += blockDim.x) {
+        const int e = t / LCT, cc = t - e * LCT, j = jb + cc;
+        if (j < j1) {
+            double* x = elem(A, lda, N, list[1 + 2 * e], j);
+#pragma unroll
+            for (int q = 0; q < N; ++q) x[q] = buf[(e * LCT + cc) * N + q];
+        }
+    }
+}
+
+// the permutation of interchanges [k0, k1) applied to column ranges
+template <int N>
+void laswp2(double* A, long long lda, int ja0, int ja1, int jb0, int jb1, int k0, int k1, const int* ipiv,
+            int* list, cudaStream_t s) {
+    if (k1 <= k0 || (ja1 <= ja0 && jb1 <= jb0)) return;
+    if (k1 - k0 > LMAXB) {
+        if (ja1 > ja0) laswp_kernel<N><<<(ja1 - ja0 + 127) / 128, 128, 0, s>>>(A, lda, ja0, ja1, k0, k1, ipiv);
+        if (jb1 > jb0) laswp_kernel<N><<<(jb1 - jb0 + 127) / 128, 128, 0, s>>>(A, lda, jb0, jb1, k0, k1, ipiv);
+        return;
+    }
+    laswp_list_kernel<<<1, 256, 0, s>>>(k0, k1, ipiv, list);
+    const size_t smem = sizeof(double) * 2 * (k1 - k0) * LCT * N;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(laswp_apply_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)(sizeof(double) * 2 * LMAXB * LCT * N));
+        attr = true;
+    }
+    if (ja1 > ja0) laswp_apply_kernel<N><<<(ja1 - ja0 + LCT - 1) / LCT, 256, smem, s>>>(A, lda, ja0, ja1, list);
+    if (jb1 > jb0) laswp_apply_kernel<N><<<(jb1 - jb0 + LCT - 1) / LCT, 256, smem, s>>>(A, lda, jb0, jb1, list);
+}
+
+// The b x b triangle of a base triangular solve, converted once to L-limb
+// floats (and the reciprocal diagonal for the upper case) in the scratch.
+template <int N>
+__global__ void __launch_bounds__(256) tri_convert_kernel(const double* T, long long ldt, int b, int lower,
+                                                          LuScratch* sc) {
+    constexpr int L = Limbs<N>::L;
+    MPF<L>* tl = reinterpret_cast<MPF<L>*>(sc->tri);
+    MPF<L>* rd = tl + BASE * BASE;
+    for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < b * b; idx += gridDim.x * blockDim.x) {
+        const int i = idx / b, k = idx - i * b;
+        const bool need = lower ? (k < i) : (k >= i);
+        const MPF<L> v = need ? mpf_from_exp<L, N>(T + ((long long)i + (long long)k * ldt) * N) : mpf_make_zero<L>();
+        tl[k * BASE + i] = v;  // column-major: a step reads one column across the rows
+        if (!lower && i == k) rd[k] = mpf_zero<L>(v) ? mpf_make_zero<L>() : mpf_recip<L>(v);
+    }
+}
+
 // X <- L^-1 X for a unit lower (lower = 1) or U^-1 X for an upper (lower = 0,
 // non-unit) b x b triangle, b <= BASE; X is b x ncols.  L-limb integer
 // floating point; a block of 32 x cpb threads owns cpb columns, thread
 // (row, column) updates its element after each pivot row is final.
 template <int N>
-__global__ void __launch_bounds__(256) trsm_base_kernel(const double* T, long long ldt, double* X,
-                                                        long long ldx, int b, int ncols, int lower) {
+__global__ void __launch_bounds__(256) trsm_base_kernel(const LuScratch* sc, double* X, long long ldx, int b,
+                                                        int ncols, int lower) {
     constexpr int L = Limbs<N>::L;
     extern __shared__ __align__(16) unsigned char smraw[];
-    MPF<L>* sl = reinterpret_cast<MPF<L>*>(smraw);   // [i][k]
+    MPF<L>* sl = reinterpret_cast<MPF<L>*>(smraw);   // [k][i]
     MPF<L>* rd = sl + BASE * BASE;                   // reciprocal diagonal (upper)
     MPF<L>* sx = rd + BASE;                          // [cc][i]
     const int cpb = blockDim.x >> 5;
     const int row = threadIdx.x & 31, cc = threadIdx.x >> 5;
     const int col = blockIdx.x * cpb + cc;
-    for (int idx = threadIdx.x; idx < b * b; idx += blockDim.x) {
-        const int i = idx / b, k = idx - i * b;
-        const bool need = lower ? (k < i) : (k >= i);
-        sl[i * BASE + k] = need ? mpf_from_exp<L, N>(T + ((long long)i + (long long)k * ldt) * N)
-                                : mpf_make_zero<L>();
-    }
-    __syncthreads();
+    const MPF<L>* tl = reinterpret_cast<const MPF<L>*>(sc->tri);
+    for (int idx = threadIdx.x; idx < BASE * BASE; idx += blockDim.x) sl[idx] = tl[idx];
     if (!lower)
-        for (int k = threadIdx.x; k < b; k += blockDim.x)
-            rd[k] = mpf_zero<L>(sl[k * BASE + k]) ? mpf_make_zero<L>() : mpf_recip<L>(sl[k * BASE + k]);
+        for (int k = threadIdx.x; k < b; k += blockDim.x) rd[k] = tl[BASE * BASE + k];
     if (row < b)
         sx[cc * BASE + row] = col < ncols ? mpf_from_exp<L, N>(X + ((long long)row + (long long)col * ldx) * N)
                                           : mpf_make_zero<L>();
@@ -579,7 +711,7 @@ __global__ void __launch_bounds__(256) trsm_base_kernel(const double* T, long lo
             __syncthreads();
         }
         if (row < b && ((lower && row > k) || (!lower && row < k)))
-            sx[cc * BASE + row] = mpf_fms<L>(sx[cc * BASE + row], sl[row * BASE + k], sx[cc * BASE + k]);
+            sx[cc * BASE + row] = mpf_fms<L>(sx[cc * BASE + row], sl[k * BASE + row], sx[cc * BASE + k]);
         __syncthreads();
     }
     if (row < b && col < ncols) mpf_to_exp<L, N>(sx[cc * BASE + row], X + ((long long)row + (long long)col * ldx) * N);
@@ -587,9 +719,10 @@ __global__ void __launch_bounds__(256) trsm_base_kernel(const double* T, long lo
 
 template <int N>
 void trsm_base(const double* T, long long ldt, double* X, long long ldx, int b, int ncols, int lower,
-               cudaStream_t s) {
+               LuScratch* sc, cudaStream_t s) {
     if (ncols <= 0 || b <= 0) return;
     constexpr int L = Limbs<N>::L;
+    tri_convert_kernel<N><<<(b * b + 255) / 256, 256, 0, s>>>(T, ldt, b, lower, sc);
     int cpb = ncols / 304;
     cpb = cpb < 1 ? 1 : (cpb > 8 ? 8 : cpb);
     const size_t smem = sizeof(MPF<L>) * (BASE * BASE + BASE + BASE * cpb);
@@ -599,7 +732,7 @@ void trsm_base(const double* T, long long ldt, double* X, long long ldx, int b, 
                              (int)(sizeof(MPF<L>) * (BASE * BASE + BASE + BASE * 8)));
         attr = true;
     }
-    trsm_base_kernel<N><<<(ncols + cpb - 1) / cpb, 32 * cpb, smem, s>>>(T, ldt, X, ldx, b, ncols, lower);
+    trsm_base_kernel<N><<<(ncols + cpb - 1) / cpb, 32 * cpb, smem, s>>>(sc, X, ldx, b, ncols, lower);
 }
 
 // Launch the cooperative base-block kernel; returns false when the slice of
@@ -655,8 +788,8 @@ void trsm_rec(Ctx& c, long long r, int b, long long j0, int ncols, bool lower) {
     if (c.rc || ncols <= 0) return;
     if (b <= BASE) {
         c.h->phase(PH_PANEL);
-        trsm_base<N>(at(c, r, r), c.lda, at(c, r, j0), c.lda, b, ncols, lower ? 1 : 0, c.h->stream);
-        c.h->count(1);
+        trsm_base<N>(at(c, r, r), c.lda, at(c, r, j0), c.lda, b, ncols, lower ? 1 : 0, c.sc, c.h->stream);
+        c.h->count(2);
         return;
     }
     const int b1 = b / 2;
@@ -724,9 +857,7 @@ int getrf_device(ozlu_handle* h, int p, int n, double* A, long long lda, int* ip
         // (P2) interchanges on the columns left and right of the panel
         h->phase(PH_OTHER);
         h->count((r0 > 0) + (r0 + b < n));
-        if (r0 > 0) laswp_kernel<N><<<(r0 + 127) / 128, 128, 0, s>>>(A, lda, 0, r0, r0, r0 + b, ipiv);
-        if (r0 + b < n)
-            laswp_kernel<N><<<(n - r0 - b + 127) / 128, 128, 0, s>>>(A, lda, r0 + b, n, r0, r0 + b, ipiv);
+        laswp2<N>(A, lda, 0, r0, r0 + b, n, r0, r0 + b, ipiv, sc->plist, s);
         if (r0 + b < n) {
             // (P3) U12 = L11^-1 A12
             trsm_rec<N>(c, r0, b, r0 + b, n - r0 - b, true);
@@ -743,17 +874,17 @@ int getrf_device(ozlu_handle* h, int p, int n, double* A, long long lda, int* ip
 
 template <int N>
 int getrs_device(ozlu_handle* h, int p, int n, int nrhs, double* LU, long long lda, const int* ipiv,
-                 double* B, long long ldb, const ozlu_opts* opts) {
+                 double* B, long long ldb, const ozlu_opts* opts, LuScratch* sc) {
     cudaStream_t s = h->stream;
     laswp_kernel<N><<<(nrhs + 127) / 128, 128, 0, s>>>(B, ldb, 0, nrhs, 0, n, ipiv);
     int rc = 0;
     auto L = [&](long long i, long long j) { return LU + (i + j * lda) * N; };
     auto X = [&](long long i) { return B + i * N; };
     h->phase(PH_PANEL);
-    h->count(1 + 2 * ((n + BASE - 1) / BASE));
+    h->count(1 + 3 * ((n + BASE - 1) / BASE));
     for (int r = 0; r < n && !rc; r += BASE) {
         const int b = BASE < n - r ? BASE : n - r;
-        trsm_base<N>(L(r, r), lda, X(r), ldb, b, nrhs, 1, s);
+        trsm_base<N>(L(r, r), lda, X(r), ldb, b, nrhs, 1, sc, s);
         if (r + b < n)
             rc = gemm_device(h, N, p, n - r - b, nrhs, b, -1, L(r + b, r), lda, X(r), ldb, 1,
                              X(r + b), ldb, opts);
@@ -761,7 +892,7 @@ int getrs_device(ozlu_handle* h, int p, int n, int nrhs, double* LU, long long l
     const int last = ((n - 1) / BASE) * BASE;
     for (int r = last; r >= 0 && !rc; r -= BASE) {
         const int b = BASE < n - r ? BASE : n - r;
-        trsm_base<N>(L(r, r), lda, X(r), ldb, b, nrhs, 0, s);
+        trsm_base<N>(L(r, r), lda, X(r), ldb, b, nrhs, 0, sc, s);
         if (r > 0)
             rc = gemm_device(h, N, p, r, nrhs, b, -1, L(0, r), lda, X(r), ldb, 1, X(0), ldb, opts);
     }
@@ -881,6 +1012,9 @@ extern "C" int ozlu_getrs(ozlu_handle* h, int nc, int p, int n, int nrhs, const 
     if (n == 0 || nrhs == 0) return OZLU_OK;
     if (cudaSetDevice(h->device) != cudaSuccess) return OZLU_ERR_CUDA;
     cudaStream_t s = h->stream;
+    LuScratch* sc;
+    int rc0 = lu_scratch(h, &sc);
+    if (rc0) return rc0;
     const bool dL = is_device_ptr(LU), dP = is_device_ptr(ipiv), dB = is_device_ptr(B);
     const size_t lbytes = sizeof(double) * nc * (size_t)lda * n;
     const size_t bbytes = sizeof(double) * nc * (size_t)ldb * nrhs;
@@ -901,9 +1035,9 @@ extern "C" int ozlu_getrs(ozlu_handle* h, int nc, int p, int n, int nrhs, const 
         }
     }
     switch (nc) {
-        case 2: rc = getrs_device<2>(h, p, n, nrhs, (double*)gL, lda, gP, gB, ldb, opts); break;
-        case 3: rc = getrs_device<3>(h, p, n, nrhs, (double*)gL, lda, gP, gB, ldb, opts); break;
-        default: rc = getrs_device<4>(h, p, n, nrhs, (double*)gL, lda, gP, gB, ldb, opts); break;
+        case 2: rc = getrs_device<2>(h, p, n, nrhs, (double*)gL, lda, gP, gB, ldb, opts, sc); break;
+        case 3: rc = getrs_device<3>(h, p, n, nrhs, (double*)gL, lda, gP, gB, ldb, opts, sc); break;
+        default: rc = getrs_device<4>(h, p, n, nrhs, (double*)gL, lda, gP, gB, ldb, opts, sc); break;
     }
     if (rc) return rc;
     if (!dB && cudaMemcpyAsync(B, gB, bbytes, cudaMemcpyDeviceToHost, s)) return OZLU_ERR_CUDA;
