@@ -53,7 +53,9 @@ enum {
 
 /* Residue back-ends of (S4) (Sec. 3.5, Table backend_origin). */
 enum {
-    OZLU_BE_AUTO = 0, /* measured choice per shape (autotuner)                        */
+    OZLU_BE_AUTO = 0, /* measured choice per shape: each feasible back-end is timed on
+                         the first call of a shape (the call then waits for the
+                         stream) and the fastest is cached in the handle          */
     OZLU_BE_INT8 = 1, /* centered residues in int8, exact int32 accumulation          */
     OZLU_BE_FP8 = 2,  /* balanced base-17 digits in E4M3, Eq. (15), fp32 accumulation */
     OZLU_BE_FP64 = 3, /* residues of ~23-bit primes in binary64, Eq. (17)             */
@@ -130,7 +132,8 @@ int ozlu_getrs(ozlu_handle* handle, int nc, int p, int n, int nrhs,
  *   1 mu  (m int32)        2 nu (n int32)
  *   3 residues of A  int8 [l][t][i][h], h < k, planes (l, t) in order
  *   4 residues of B  int8 [l][t][j][h]
- *   5 t values      uint8 [gi][l][j][i] (column-major m x n per plane)
+ *   5 t values      uint8 [gi][l][j][i] (column-major m x n per plane);
+ *                   uint32 for the binary64 back-end
  *   6 device error word (int32): 0, or OZLU_ERR_TIMEOUT when a bounded
  *     wait inside a tensor-core GEMM gave up (sticky until the workspace
  *     is reallocated)
@@ -153,6 +156,8 @@ typedef struct {
     double convert_ms, gemm_ms, crt_ms, panel_ms, other_ms;
     long long gemm_launches, crt_launches, panel_launches, launches;
     double gemm_ops, crt_bytes, convert_bytes;
+    int last_backend;  /* back-end of the last residue GEMM (after autotuning) */
+    int pad_;
 } ozlu_stats;
 int ozlu_set_timing(ozlu_handle* handle, int enable);
 int ozlu_get_stats(ozlu_handle* handle, ozlu_stats* out);

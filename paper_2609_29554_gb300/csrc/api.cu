@@ -67,7 +67,77 @@ int plan_for(ozlu_handle* h, int p, int K, const ozlu_opts* o, const Plan** out,
 
 static size_t align_up(size_t v) { return (v + 255) / 256 * 256; }
 
+// Measured choice of the residue back-end (Sec. 3.5 guideline: the format
+// maximising bits per modulus times engine throughput, which the paper
+// concludes can only be decided by measuring at the actual size).  Each
+// feasible back-end whose model time (residue ops / engine rate) is within
+// 4x of the best model is run once on the caller's operands into a scratch C
+// and timed with events; the fastest is cached per (nc, p, k, options,
+// log2 m, log2 n).  The first call of a new shape therefore waits for the
+// stream.
+int autotune(ozlu_handle* h, int nc, int p, int m, int n, int k, const double* A, long long lda,
+             const double* B, long long ldb, const ozlu_opts& o, int* out) {
+    auto lg = [](int v) { int r = 0; while ((1 << r) < v) ++r; return r; };
+    const auto key = std::make_tuple(nc, p, k, o.nslice * 1000000 + o.extra_groups * 1000 + o.g_ex,
+                                     lg(m), lg(n));
+    auto it = h->tuned.find(key);
+    if (it != h->tuned.end()) {
+        *out = it->second;
+        return OZLU_OK;
+    }
+    // engine rates in residue-product tera-ops per second (GB300 measurements)
+    const int cand[4] = {OZLU_BE_FP16, OZLU_BE_FP8, OZLU_BE_INT8, OZLU_BE_FP64};
+    const double rate[4] = {600.0, 1700.0 / 3.0, 150.0, 1.0};
+    double model[4];
+    bool ok[4];
+    double best_model = 1e300;
+    for (int c = 0; c < 4; ++c) {
+        ozlu_opts t = o;
+        t.backend = cand[c];
+        Plan pl;
+        ok[c] = make_plan(p, k, &t, pl) == OZLU_OK;
+        model[c] = ok[c] ? 2.0 * m * n * (double)k * pl.N * pl.pair_terms / (rate[c] * 1e12) : 1e300;
+        if (ok[c] && model[c] < best_model) best_model = model[c];
+    }
+    // scratch C
+    const size_t cbytes = sizeof(double) * nc * (size_t)m * n;
+    int rc = h->tune_ws.ensure(cbytes);
+    if (rc) return rc;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int choice = OZLU_BE_INT8;
+    const bool timing = h->timing;
+    h->timing = false;
+    for (int c = 0; c < 4; ++c) {
+        if (!ok[c] || model[c] > 4.0 * best_model) continue;
+        ozlu_opts t = o;
+        t.backend = cand[c];
+        cudaEventRecord(e0, h->stream);
+        rc = gemm_device(h, nc, p, m, n, k, 1, A, lda, B, ldb, 0, (double*)h->tune_ws.base, m, &t);
+        cudaEventRecord(e1, h->stream);
+        if (rc == OZLU_ERR_UNSUPPORTED) continue;
+        if (rc) break;
+        cudaEventSynchronize(e1);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; choice = cand[c]; }
+    }
+    h->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc && rc != OZLU_ERR_UNSUPPORTED) return rc;
+    h->tuned[key] = choice;
+    h->stats.last_backend = choice;
+    *out = choice;
+    return OZLU_OK;
+}
+
 // The device part of one GEMM, all pointers on the device.
+int autotune(ozlu_handle* h, int nc, int p, int m, int n, int k, const double* A, long long lda,
+             const double* B, long long ldb, const ozlu_opts& o, int* out);
+
 int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, const double* A,
                 long long lda, const double* B, long long ldb, int beta, double* C,
                 long long ldc, const ozlu_opts* opts) {
@@ -84,15 +154,18 @@ int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, c
     ozlu_opts o;
     memset(&o, 0, sizeof o);
     if (opts) o = *opts;
-    if (o.backend == OZLU_BE_AUTO) o.backend = OZLU_BE_INT8;
+    if (o.backend == OZLU_BE_AUTO) {
+        const int rc0 = autotune(h, nc, p, m, n, k, A, lda, B, ldb, o, &o.backend);
+        if (rc0) return rc0;
+    }
     const Plan* pl;
     const DevTable* tab;
     int rc = plan_for(h, p, k, &o, &pl, &tab);
     if (rc) return rc;
     const int be = pl->backend;
-    if (be == OZLU_BE_FP64) return OZLU_ERR_UNSUPPORTED;
-    const int mode = be == OZLU_BE_INT8 ? 0 : (be == OZLU_BE_FP8 ? 1 : 2);
-    const int P = mode == 1 ? 3 : 1, esz = mode == 2 ? 2 : 1;
+    const int mode = be == OZLU_BE_INT8 ? 0 : be == OZLU_BE_FP8 ? 1 : be == OZLU_BE_FP16 ? 2 : 3;
+    const int P = mode == 1 ? 3 : 1, esz = mode == 2 ? 2 : (mode == 3 ? 8 : 1);
+    const int tsz = mode == 3 ? 4 : 1;  // bytes per t value
     const int Mpad = (m + 127) / 128 * 128, Npad = (n + 127) / 128 * 128;
     const int Kpad = pl->Kpad;
     GemmLayout& L = h->last;
@@ -103,7 +176,7 @@ int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, c
     L.nu = off; off = align_up(off + sizeof(int) * n);
     L.ra = off; off = align_up(off + (size_t)pl->N * pl->S * P * Mpad * Kpad * esz);
     L.rb = off; off = align_up(off + (size_t)pl->N * pl->S * P * Npad * Kpad * esz);
-    L.t = off;  off = align_up(off + (size_t)pl->G * pl->N * m * n);
+    L.t = off;  off = align_up(off + (size_t)pl->G * pl->N * m * n * tsz);
     L.err = off; off = align_up(off + sizeof(int));
     const bool fresh = h->ws.cap < off;
     rc = h->ws.ensure(off);
@@ -128,15 +201,18 @@ int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, c
     h->phase(PH_GEMM);
     if (mode == 0) {
         launch_gemm_imma((const int8_t*)RA, (const int8_t*)RB, m, n, Mpad, Npad, Kpad, *tab, T, s);
+    } else if (mode == 3) {
+        launch_gemm_f64((const double*)RA, (const double*)RB, m, n, Mpad, Npad, Kpad, *tab, (uint32_t*)T, s);
     } else {
         rc = launch_gemm_tc05(mode == 1, RA, RB, m, n, Mpad, Npad, Kpad, *tab, T, derr, s);
         if (rc) return rc;
     }
     h->phase(PH_CRT);
-    launch_crt(T, m, n, mu, nu, *tab, nc, alpha, beta, C, ldc, s);
+    launch_crt(T, mode == 3, m, n, mu, nu, *tab, nc, alpha, beta, C, ldc, s);
     h->phase(prev);
     h->stats.gemm_launches += 1;
     h->stats.crt_launches += 1;
+    h->stats.last_backend = be;
     h->stats.gemm_ops += 2.0 * m * n * (double)k * pl->N * pl->pair_terms * P;
     h->stats.crt_bytes += (double)pl->G * pl->N * m * n + 8.0 * nc * m * n * (beta ? 2 : 1);
     h->stats.convert_bytes += 8.0 * nc * ((double)m * k + (double)k * n) +
@@ -212,6 +288,7 @@ int ozlu_destroy(ozlu_handle* h) {
     cudaStreamSynchronize(h->stream);
     h->ws.release();
     h->stage.release();
+    h->tune_ws.release();
     if (h->lu_scratch) cudaFree(h->lu_scratch);
     if (h->coop_scratch) cudaFree(h->coop_scratch);
     for (auto& e : h->pool) cudaEventDestroy(e);
@@ -317,7 +394,7 @@ int ozlu_debug_fetch(ozlu_handle* h, int what, void* dst, size_t bytes) {
         return OZLU_OK;
     }
     if (what == 5) {
-        const size_t need = (size_t)L.G * L.N * L.m * L.n;
+        const size_t need = (size_t)L.G * L.N * L.m * L.n * (L.backend == OZLU_BE_FP64 ? 4 : 1);
         if (bytes < need) return -4;
         return cuda_rc(cudaMemcpy(dst, base + L.t, need, cudaMemcpyDeviceToHost));
     }

@@ -80,10 +80,31 @@ __device__ __forceinline__ int centered_residue(const uint32_t (&mag)[MAXD], boo
 //   B side (is_b = 1): element (h, r) of a K x R matrix, plane [l][t][r][h]
 // Threads cover the padded range [0, Rpad) x [0, Kpad) and write zeros there.
 // store residue r of plane (l, t) at element offset off, in the back-end's encoding
+// Residue modulo a binary64-back-end prime (m < 2^27): 64-bit sum of the
+// half products, then one 64-bit remainder.
+template <int H>
+__device__ __forceinline__ int centered_residue64(const uint32_t (&mag)[MAXD], bool neg,
+                                                  const DevTable& tab, int l) {
+    const uint64_t m = (uint64_t)tab.mod[l];
+    uint64_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < H; ++j) {
+        const uint64_t half = (mag[j >> 1] >> (16 * (j & 1))) & 0xffffu;
+        acc += half * tab.pow16[l][j];
+    }
+    uint64_t r = acc % m;
+    if (neg && r) r = m - r;
+    long long c = (long long)r;
+    if (c > (long long)(m - 1) / 2) c -= (long long)m;
+    return (int)c;
+}
+
 template <int MODE>
 __device__ __forceinline__ void put_residue(void* planes, size_t plane, int l, int S, int t,
                                             size_t off, int r) {
-    if (MODE == 0) {
+    if (MODE == 3) {
+        ((double*)planes)[(size_t)(l * S + t) * plane + off] = (double)r;
+    } else if (MODE == 0) {
         ((int8_t*)planes)[(size_t)(l * S + t) * plane + off] = (int8_t)r;
     } else if (MODE == 1) {
         // Eq. (15): r = 17 d1 + d0, d1 = round(r / 17) (no ties: 17 is odd)
@@ -170,7 +191,7 @@ __global__ void __launch_bounds__(256) convert_kernel(
             for (int k2 = 0; k2 < MAXD; ++k2) D[k2] = T[k2];
         }
         for (int l = 0; l < tab.N; ++l) {
-            const int res = centered_residue<H>(D, neg, tab, l);
+            const int res = MODE == 3 ? centered_residue64<H>(D, neg, tab, l) : centered_residue<H>(D, neg, tab, l);
             put_residue<MODE>(planes, plane, l, S, t, off, res);
         }
     }
@@ -210,6 +231,7 @@ void launch_convert(const double* X, long long ld, int nc, int rows, int cols, b
         OZLU_CONV_M(0)
         OZLU_CONV_M(1)
         OZLU_CONV_M(2)
+        OZLU_CONV_M(3)
 #undef OZLU_CONV_M
 #undef OZLU_CONV
         default:

@@ -187,8 +187,8 @@ __device__ __forceinline__ void wide_round_out(const Wide& X, bool neg, int E, i
     }
 }
 
-template <int WG>
-__global__ void __launch_bounds__(CT) crt_kernel(const uint8_t* __restrict__ T, int m, int n,
+template <int WG, typename TT>
+__global__ void __launch_bounds__(CT) crt_kernel(const TT* __restrict__ T, int m, int n,
                                                  const int* __restrict__ mu, const int* __restrict__ nu,
                                                  const __grid_constant__ DevTable tab, int nc, int alpha,
                                                  int beta, double* __restrict__ C, long long ldc) {
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(CT) crt_kernel(const uint8_t* __restrict__ T, 
 #pragma unroll
         for (int w = 0; w < WG; ++w) acc[w] = 0;
         float F = 0.0f;
-        const uint8_t* tp = T + (size_t)gi * tab.N * mn + e;
+        const TT* tp = T + (size_t)gi * tab.N * mn + e;
         for (int l = 0; l < tab.N; ++l) {
             const uint32_t t = tp[(size_t)l * mn];
 #pragma unroll
@@ -252,19 +252,17 @@ __global__ void __launch_bounds__(CT) crt_kernel(const uint8_t* __restrict__ T, 
     for (int c = 0; c < nc; ++c) cp[c] = out[c];
 }
 
-template <int WG>
-void launch_wg(const uint8_t* T, int m, int n, const int* mu, const int* nu, const DevTable& tab, int nc,
+template <int WG, typename TT>
+void launch_wg(const TT* T, int m, int n, const int* mu, const int* nu, const DevTable& tab, int nc,
                int alpha, int beta, double* C, long long ldc, cudaStream_t s) {
     const long long mn = (long long)m * n;
-    crt_kernel<WG><<<(unsigned)((mn + CT - 1) / CT), CT, 0, s>>>(T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc);
+    crt_kernel<WG, TT><<<(unsigned)((mn + CT - 1) / CT), CT, 0, s>>>(T, m, n, mu, nu, tab, nc, alpha, beta, C,
+                                                                     ldc);
 }
 
-}  // namespace
-
-void launch_crt(const uint8_t* T, int m, int n, const int* mu, const int* nu, const DevTable& tab, int nc,
-                int alpha, int beta, double* C, long long ldc, cudaStream_t s) {
-    const long long mn = (long long)m * n;
-    if (mn == 0) return;
+template <typename TT>
+void launch_tt(const TT* T, int m, int n, const int* mu, const int* nu, const DevTable& tab, int nc, int alpha,
+               int beta, double* C, long long ldc, cudaStream_t s) {
     switch (tab.WG) {
         case 1: case 2: case 3: case 4: launch_wg<4>(T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s); break;
         case 5: launch_wg<5>(T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s); break;
@@ -274,8 +272,24 @@ void launch_crt(const uint8_t* T, int m, int n, const int* mu, const int* nu, co
         case 9: launch_wg<9>(T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s); break;
         case 10: launch_wg<10>(T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s); break;
         case 11: launch_wg<11>(T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s); break;
-        default: launch_wg<12>(T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s); break;
+        case 12: launch_wg<12>(T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s); break;
+        case 13: launch_wg<13>(T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s); break;
+        case 14: launch_wg<14>(T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s); break;
+        case 15: launch_wg<15>(T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s); break;
+        default: launch_wg<16>(T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s); break;
     }
+}
+
+}  // namespace
+
+void launch_crt(const void* T, bool t32, int m, int n, const int* mu, const int* nu, const DevTable& tab, int nc,
+                int alpha, int beta, double* C, long long ldc, cudaStream_t s) {
+    const long long mn = (long long)m * n;
+    if (mn == 0) return;
+    if (t32)
+        launch_tt<uint32_t>((const uint32_t*)T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s);
+    else
+        launch_tt<uint8_t>((const uint8_t*)T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s);
 }
 
 }  // namespace ozlu

@@ -216,6 +216,6 @@ extern "C" int ozlu_gemm_noalloc(int nc, int p, int m, int n, int k, int alpha, 
     launch_convert(A, lda, nc, m, k, false, mu, tab, Kpad, Mpad, RA, 0, s);
     launch_convert(B, ldb, nc, k, n, true, nu, tab, Kpad, Npad, RB, 0, s);
     launch_gemm_imma(RA, RB, m, n, Mpad, Npad, Kpad, tab, T, s);
-    launch_crt(T, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s);
+    launch_crt(T, false, m, n, mu, nu, tab, nc, alpha, beta, C, ldc, s);
     return cudaGetLastError() == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
 }

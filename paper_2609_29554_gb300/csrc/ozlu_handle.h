@@ -35,6 +35,8 @@ struct ozlu_handle {
     cudaStream_t stream = nullptr;
     ozlu::Workspace ws;     // GEMM intermediates
     ozlu::Workspace stage;  // host-argument staging
+    ozlu::Workspace tune_ws;  // scratch output of the back-end autotuner
+    std::map<std::tuple<int, int, int, int, int, int>, int> tuned;  // shape key -> back-end
     std::map<std::tuple<int, int, int, int, int, int>, ozlu::PlanEntry> plans;
     ozlu::GemmLayout last;
     size_t err_off = (size_t)-1;  // workspace offset of the device error word

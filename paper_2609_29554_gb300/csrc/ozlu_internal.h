@@ -13,7 +13,7 @@ namespace ozlu {
 
 constexpr int MAXMOD = 64;       // moduli per plan (INT8 set has 54)
 constexpr int MAXH = 16;         // 16-bit halves of one balanced digit (w < 256)
-constexpr int MAXWG = 12;        // 32-bit words of one digit-group integer S_g
+constexpr int MAXWG = 16;        // 32-bit words of one digit-group integer S_g
 constexpr int WACC = 16;         // 32-bit words of the fused output window
 constexpr int WINDOW_BITS = 510; // window width above the grid 2^E (sign bit spare)
 constexpr int MAXWX = 12;        // 32-bit words of one Q-bit fixed-point input
@@ -55,7 +55,8 @@ void launch_col_shifts(const double* B, long long ldb, int nc, int k, int n, int
 // (S2)+(S3) fused: expansions -> Q-bit integers -> S digits -> residue planes.
 // A side: planes [l][t][Mpad][Kpad] (row i, K contiguous); B side: [l][t][Npad][Kpad].
 // mode 0: int8 residues (1 plane); 1: E4M3 base-17 digits d0, d1, d0+d1 (3 planes);
-// 2: binary16 residues (1 plane, 2-byte elements).  Plane index (l * S + t) * P + p.
+// 2: binary16 residues (1 plane, 2-byte elements); 3: binary64 residues (8-byte).
+// Plane index (l * S + t) * P + p.
 void launch_convert(const double* X, long long ld, int nc, int rows, int cols,
                     bool is_b, const int* shifts, const DevTable& tab, int Kpad,
                     int Rpad, void* planes, int mode, cudaStream_t s);
@@ -66,8 +67,12 @@ int launch_gemm_tc05(bool fp8, const void* RA, const void* RB, int m, int n, int
 void launch_gemm_imma(const int8_t* RA, const int8_t* RB, int m, int n, int Mpad,
                       int Npad, int Kpad, const DevTable& tab, uint8_t* T,
                       cudaStream_t s);
+// (S4) binary64 residue GEMMs; t values as 32-bit words
+void launch_gemm_f64(const double* RA, const double* RB, int m, int n, int Mpad, int Npad, int Kpad,
+                     const DevTable& tab, uint32_t* T, cudaStream_t s);
 // (S5)+(S6): CRT per digit group, recombination, fused beta*C + alpha*AB, rounding.
-void launch_crt(const uint8_t* T, int m, int n, const int* mu, const int* nu,
+// t values are bytes (INT8/FP8/FP16 moduli <= 255) or 32-bit words (t32, binary64).
+void launch_crt(const void* T, bool t32, int m, int n, const int* mu, const int* nu,
                 const DevTable& tab, int nc, int alpha, int beta, double* C,
                 long long ldc, cudaStream_t s);
 

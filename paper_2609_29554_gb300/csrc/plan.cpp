@@ -140,6 +140,8 @@ int make_plan(int p, int K, const ozlu_opts* o, Plan& out) {
         pl.pint_bits = w * (2 * S - 2 - pl.g0) + pl.sbar_bits;
         pl.WX = (pl.Q + 1 + 31) / 32;
         pl.H = (w + 1 + 15) / 16;
+        // 32-bit t values of the binary64 back-end: sum t M_l < 2^64 needs N <= 32
+        if (be == OZLU_BE_FP64 && N > 32) return OZLU_ERR_CAPACITY;
         if (N > MAXMOD || pl.WG > MAXWG || pl.WX > MAXWX || pl.H > MAXH || pl.G > MAXG ||
             pl.pint_bits + 2 > WINDOW_BITS)
             return OZLU_ERR_CAPACITY;

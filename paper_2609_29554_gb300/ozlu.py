@@ -48,7 +48,8 @@ class ozlu_stats(ctypes.Structure):
                 ("other_ms", ctypes.c_double), ("gemm_launches", ctypes.c_longlong),
                 ("crt_launches", ctypes.c_longlong), ("panel_launches", ctypes.c_longlong),
                 ("launches", ctypes.c_longlong), ("gemm_ops", ctypes.c_double),
-                ("crt_bytes", ctypes.c_double), ("convert_bytes", ctypes.c_double)]
+                ("crt_bytes", ctypes.c_double), ("convert_bytes", ctypes.c_double),
+                ("last_backend", ctypes.c_int), ("pad_", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p

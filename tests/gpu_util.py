@@ -35,7 +35,10 @@ def host(t, rows):
 
 
 def gpu_gemm(A, B, p=0, alpha=1, beta=0, C=None, opts=None, debug=False):
+    """ozlu_gemm through the C ABI; the INT8 back-end unless opts says otherwise."""
     h = handle()
+    if opts is None:
+        opts = ozlu.make_opts("int8")
     m, k, nc = A.shape
     n = B.shape[1]
     dA, dB = dev(A), dev(B)
