@@ -43,10 +43,14 @@ def parse():
     ap.add_argument("--nc", type=int, default=4)
     ap.add_argument("--log10cond", type=float, default=40.0)
     ap.add_argument("--seed", type=int, default=4)
-    ap.add_argument("--backend", default="int8")
+    ap.add_argument("--backend", default="auto")
+    ap.add_argument("--compare", action="store_true",
+                    help="also time the single-instance INT8 Ozaki-II LU and the native "
+                         "(blocked-naive) expansion LU on the same matrix")
+    ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-sample-n", type=int, default=224)
+    ap.add_argument("--cpu-sample-n", type=int, default=352)
     return ap.parse_args()
 
 
@@ -188,6 +192,111 @@ def run_reference(a):
     return 0
 
 
+# ------------------------------------------------------------------ roofline --
+# Peaks for the integer and binary64 pipes come from this repository's own
+# probes on a GB300 (register-only loops): IMAD 18.9 T/s,
+# mma.sync s8 151.6 TOPS.  Tensor-core peaks scale the measured bf16 number
+# by the nominal ratios (fp8 = 2x, fp16 = 1x).
+IMAD_PEAK = 18.9        # T IMAD/s
+IMMA_PEAK = 151.6       # TOPS (mma.sync s8)
+
+
+def roofline(st, a, peaks, src):
+    steps = a.steps
+    phases = {"gemm": st.gemm_ms, "crt": st.crt_ms, "convert": st.convert_ms,
+              "panel": st.panel_ms, "trsm": st.trsm_ms}
+    dom = max(phases, key=phases.get)
+    be = {1: "int8", 2: "fp8", 3: "fp64", 4: "fp16"}.get(st.last_backend, "int8")
+    n, nc = a.n, a.nc
+    L = {2: 4, 3: 6, 4: 8}[nc]
+    if dom == "gemm":
+        achieved = st.gemm_ops / (st.gemm_ms * 1e-3) / 1e12
+        peak = {"int8": IMMA_PEAK, "fp8": 2 * peaks["bf16_tflops"], "fp16": peaks["bf16_tflops"],
+                "fp64": 1.0}[be]
+        r = {"kernel": {"int8": "gemm_imma_kernel", "fp64": "gemm_f64_kernel"}.get(be, "gemm_tc05_kernel"),
+             "bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+             "peak_source": src if be in ("fp8", "fp16") else "own probe"}
+    elif dom == "convert":
+        achieved = st.convert_bytes / (st.convert_ms * 1e-3) / 1e9
+        r = {"kernel": "convert_kernel", "bound": "hbm", "achieved": achieved,
+             "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_source": src}
+    elif dom == "crt":
+        achieved = st.crt_bytes / (st.crt_ms * 1e-3) / 1e9
+        r = {"kernel": "crt_kernel", "bound": "hbm", "achieved": achieved,
+             "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_source": src}
+    else:
+        # limb products of the L-limb panel arithmetic: about n^2 BASE / 4 fused
+        # multiply-subtracts per factorisation (base blocks of 32 columns), L^2 IMADs each
+        fms = n * n * 32 / 4.0
+        achieved = fms * L * L * steps / (phases[dom] * 1e-3) / 1e12
+        r = {"kernel": "base_block_coop_kernel" if dom == "panel" else "trsm_base_kernel",
+             "bound": "alu", "achieved": achieved, "peak": IMAD_PEAK, "unit": "T IMAD/s",
+             "peak_source": "own IMAD probe"}
+    r["frac"] = r["achieved"] / r["peak"]
+    r["traffic"] = None
+    r["phase_ms_per_step"] = {k: v / steps for k, v in phases.items()}
+    return r
+
+
+def accuracy(ozlu, h, A0, LU, ipiv, n, nc, opts):
+    """Backward error max|PA - LU| / max|A| and the solution error of A x = A 1.
+
+    Both products use the Ozaki-II GEMM itself (single rounding at p bits), so
+    the figures are accurate down to about 2^-p relative.
+    """
+    import numpy as np
+    import torch
+    piv = ipiv.cpu().numpy() - 1
+    perm = np.arange(n)
+    for k in range(n):
+        perm[k], perm[piv[k]] = perm[piv[k]], perm[k]
+    idx = torch.from_numpy(perm).cuda()
+    PA = A0[:, idx, :].contiguous()                       # rows permuted (dim 1)
+    rows = torch.arange(n, device="cuda").view(1, n)
+    cols = torch.arange(n, device="cuda").view(n, 1)
+    Lm = torch.where((rows > cols).unsqueeze(-1), LU, torch.zeros_like(LU))
+    Lm[:, :, 0] += (rows == cols).to(torch.float64)
+    Um = torch.where((rows <= cols).unsqueeze(-1), LU, torch.zeros_like(LU))
+    R = PA
+    ozlu.ozlu_gemm(h, nc, 0, n, n, n, -1, Lm, n, Um, n, 1, R, n, opts)
+    ones = torch.zeros((1, n, nc), dtype=torch.float64, device="cuda")
+    ones[:, :, 0] = 1.0
+    b = torch.zeros_like(ones)
+    ozlu.ozlu_gemm(h, nc, 0, n, 1, n, 1, A0, n, ones, n, 0, b, n, opts)
+    x = b.clone()
+    ozlu.ozlu_getrs(h, nc, 0, n, 1, LU, n, ipiv, x, n, opts)
+    torch.cuda.synchronize()
+    back = float(R[..., 0].abs().max() / A0[..., 0].abs().max())
+    d = (x[0, :, 0] - 1.0) + x[0, :, 1:].sum(-1)
+    err = float(d.abs().max())
+    import math
+    return {"backward_error": back, "solution_max_abs_error": err,
+            "solution_correct_bits": (-math.log2(err) if err > 0 else None),
+            "how": "products by the Ozaki-II GEMM at p bits; b = A * ones"}
+
+
+def compare(ozlu, h, A0, A, ipiv, info, n, nb, nc, a):
+    """Single-instance INT8 Ozaki-II LU and the native blocked-naive LU (same matrix)."""
+    import torch
+    out = {}
+    for name, opts in (("ozaki2_int8_single_instance", ozlu.make_opts("int8")),
+                       ("native_blocked_expansion_lu", ozlu.make_opts("int8", native=1))):
+        A.copy_(A0)
+        ozlu.ozlu_getrf(h, nc, 0, n, A, n, ipiv, nb, info, opts)   # warm-up
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        A.copy_(A0)
+        e0.record()
+        ozlu.ozlu_getrf(h, nc, 0, n, A, n, ipiv, nb, info, opts)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[name] = {"value": 2.0 * n ** 3 / 3.0 / (ms * 1e-3) / 1e9, "unit": "Gflop/s", "ms": ms,
+                     "accuracy": accuracy(ozlu, h, A0, A, ipiv, n, nc, opts)}
+    return out
+
+
 # ------------------------------------------------------------------ ozlu ---
 def main():
     a = parse()
@@ -241,40 +350,13 @@ def main():
     assert int(info.item()) == 0, "singular pivot in the benchmark matrix"
 
     peaks, src = measured_peaks()
-    # dominant phase and its roofline
-    phases = {"gemm": st.gemm_ms, "crt": st.crt_ms, "convert": st.convert_ms, "panel": st.panel_ms}
-    dom = max(phases, key=phases.get)
-    steps = a.steps
-    if dom == "gemm":
-        # INT8 residue GEMMs run on mma.sync; our measured IMMA throughput is the peak
-        achieved = st.gemm_ops / (st.gemm_ms * 1e-3) / 1e12
-        roof = {"kernel": "gemm_imma_kernel", "bound": "tensor", "achieved": achieved,
-                "peak": 151.6, "unit": "TOPS", "peak_source": "own mma.sync s8 probe"}
-    elif dom == "crt":
-        achieved = st.crt_bytes / (st.crt_ms * 1e-3) / 1e9
-        roof = {"kernel": "crt_kernel", "bound": "hbm", "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_source": src}
-    elif dom == "convert":
-        achieved = st.convert_bytes / (st.convert_ms * 1e-3) / 1e9
-        roof = {"kernel": "convert_kernel", "bound": "hbm", "achieved": achieved,
-                "peak": peaks["hbm_gbs"], "unit": "GB/s", "peak_source": src}
-    else:
-        # expansion arithmetic in FP64; peak = our measured FP64 FMA rate
-        qd_fma_flops = {2: 25.0, 3: 60.0, 4: 110.0}[nc]
-        panel_fma = n * n * 32 / 4.0 * 2          # ~n^2 BASE/4 per factor and solve
-        achieved = panel_fma * qd_fma_flops * steps / (st.panel_ms * 1e-3) / 1e12
-        roof = {"kernel": "scale_update_kernel/trsm_base_kernel", "bound": "alu",
-                "achieved": achieved, "peak": 1.01, "unit": "TFLOP/s",
-                "peak_source": "own FP64 FMA probe"}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
-    roof["phase_ms_per_step"] = {k: v / steps for k, v in phases.items()}
-
     line = {"metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": world,
             "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(a), "roofline": roof,
+            "data": "synthetic", "config": workload_config(a),
+            "roofline": roofline(st, a, peaks, src),
             "gpu_launches": int(st.launches), "clocks": clk.summary()}
+    line["config"]["last_backend"] = {1: "int8", 2: "fp8", 3: "fp64", 4: "fp16"}.get(st.last_backend)
 
     if not a.no_e2e:
         # the same LU through the C ABI with host buffers (pinned): copies inside
@@ -297,6 +379,10 @@ def main():
                        "h2d_bytes_per_step": int(8 * nc * n * n),
                        "d2h_bytes_per_step": int(8 * nc * n * n + 4 * n + 4)}
 
+    if rank == 0 and not a.no_accuracy:
+        line["accuracy"] = accuracy(ozlu, h, A0, A, ipiv, n, nc, opts)
+    if rank == 0 and a.compare:
+        line["comparisons"] = compare(ozlu, h, A0, A, ipiv, info, n, nb, nc, a)
     if rank == 0 and not a.no_cpu_baseline:
         v, dt = oracle_lu_rate(a.cpu_sample_n, nc, a.log10cond, a.seed)
         line["cpu_baseline"] = {"value": v, "unit": "Gflop/s", "cores": 1, "kind": "oracle",

@@ -68,7 +68,10 @@ typedef struct {
     int nslice;       /* S override (Sec. 3.2); 0 = smallest feasible S            */
     int extra_groups; /* digit groups kept below S-1 (Sec. 3.2, cancellation)      */
     int g_ex;         /* extra guard bits in the slack of Sec. 3.2                 */
-    int reserved[12];
+    int native;       /* ozlu_getrf only: 1 = trailing update (P4) by per-element
+                         multiply-adds in expansion arithmetic, the "blocked naive"
+                         comparison of Sec. 3.4 (panels unchanged)                */
+    int reserved[11];
 } ozlu_opts;
 
 /* Plan of one Ozaki-II GEMM (Sec. 3.2 "Determining w and N"). */
@@ -148,7 +151,9 @@ int ozlu_debug_fetch(ozlu_handle* handle, int what, void* dst, size_t bytes);
  *   convert_ms  (S1)-(S3) exponents, conversion and residues
  *   gemm_ms     (S4) residue GEMMs with the modular epilogue
  *   crt_ms      (S5)-(S6) CRT, recombination and rounding
- *   panel_ms    (P1)-(P3) expansion-arithmetic kernels of the LU
+ *   panel_ms    (P1) base-block panel kernels of the LU
+ *   trsm_ms     (P3) and getrs base triangular-solve kernels
+ *   other_ms    row interchanges (P2)
  * launches counts every kernel the library launched; gemm_ops, crt_bytes and
  * convert_bytes are the algorithmic work of those phases (tensor operations
  * 2 M N K per residue product, and the bytes each phase must move). */
@@ -158,6 +163,7 @@ typedef struct {
     double gemm_ops, crt_bytes, convert_bytes;
     int last_backend;  /* back-end of the last residue GEMM (after autotuning) */
     int pad_;
+    double trsm_ms;
 } ozlu_stats;
 int ozlu_set_timing(ozlu_handle* handle, int enable);
 int ozlu_get_stats(ozlu_handle* handle, ozlu_stats* out);

@@ -255,7 +255,7 @@ void ozlu_handle::resolve_times() {
         float ms = 0;
         cudaEventElapsedTime(&ms, mk.second.first, mk.second.second);
         double* dst[] = {&stats.convert_ms, &stats.gemm_ms, &stats.crt_ms, &stats.panel_ms,
-                         &stats.other_ms};
+                         &stats.other_ms, &stats.trsm_ms};
         *dst[mk.first] += ms;
     }
     marks.clear();

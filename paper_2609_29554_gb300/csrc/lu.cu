@@ -664,6 +664,45 @@ void laswp2(double* A, long long lda, int ja0, int ja1, int jb0, int jb1, int k0
     if (jb1 > jb0) laswp_apply_kernel<N><<<(jb1 - jb0 + LCT - 1) / LCT, 256, smem, s>>>(A, lda, jb0, jb1, list);
 }
 
+// Native trailing update for the blocked-naive comparison (Sec. 3.4):
+// C -= A B with every multiply-add rounded in expansion arithmetic (binary64
+// TwoSum / TwoProd), 16 x 16 outputs per block, A and B tiles in shared memory.
+template <int N>
+__global__ void __launch_bounds__(256) naive_update_kernel(const double* A, long long lda, const double* B,
+                                                           long long ldb, double* C, long long ldc, int m,
+                                                           int n, int k) {
+    __shared__ double sa[16][16][N];
+    __shared__ double sb[16][16][N];
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int i = blockIdx.x * 16 + tx, j = blockIdx.y * 16 + ty;
+    Exp<N> acc;
+    if (i < m && j < n) acc = load<N>(C + ((long long)i + (long long)j * ldc) * N);
+    for (int h0 = 0; h0 < k; h0 += 16) {
+        {
+            const int ii = blockIdx.x * 16 + tx, hh = h0 + ty;
+#pragma unroll
+            for (int q = 0; q < N; ++q)
+                sa[ty][tx][q] = (ii < m && hh < k) ? A[((long long)ii + (long long)hh * lda) * N + q] : 0.0;
+            const int hb = h0 + tx, jj = blockIdx.y * 16 + ty;
+#pragma unroll
+            for (int q = 0; q < N; ++q)
+                sb[ty][tx][q] = (hb < k && jj < n) ? B[((long long)hb + (long long)jj * ldb) * N + q] : 0.0;
+        }
+        __syncthreads();
+        if (i < m && j < n) {
+            const int hmax = min(16, k - h0);
+            for (int h = 0; h < hmax; ++h) {
+                Exp<N> a, b;
+#pragma unroll
+                for (int q = 0; q < N; ++q) { a.x[q] = sa[h][tx][q]; b.x[q] = sb[ty][h][q]; }
+                acc = fms<N>(acc, a, b);
+            }
+        }
+        __syncthreads();
+    }
+    if (i < m && j < n) store<N>(C + ((long long)i + (long long)j * ldc) * N, acc);
+}
+
 // The b x b triangle of a base triangular solve, converted once to L-limb
 // floats (and the reciprocal diagonal for the upper case) in the scratch.
 template <int N>
@@ -787,7 +826,7 @@ template <int N>
 void trsm_rec(Ctx& c, long long r, int b, long long j0, int ncols, bool lower) {
     if (c.rc || ncols <= 0) return;
     if (b <= BASE) {
-        c.h->phase(PH_PANEL);
+        c.h->phase(PH_TRSM);
         trsm_base<N>(at(c, r, r), c.lda, at(c, r, j0), c.lda, b, ncols, lower ? 1 : 0, c.sc, c.h->stream);
         c.h->count(2);
         return;
@@ -862,9 +901,17 @@ int getrf_device(ozlu_handle* h, int p, int n, double* A, long long lda, int* ip
             // (P3) U12 = L11^-1 A12
             trsm_rec<N>(c, r0, b, r0 + b, n - r0 - b, true);
             // (P4) A22 <- A22 - L21 U12
-            if (!c.rc)
+            if (!c.rc && opts && opts->native) {
+                h->phase(PH_GEMM);
+                const int mm = n - r0 - b;
+                dim3 grid((mm + 15) / 16, (mm + 15) / 16);
+                naive_update_kernel<N><<<grid, 256, 0, s>>>(at(c, r0 + b, r0), lda, at(c, r0, r0 + b), lda,
+                                                            at(c, r0 + b, r0 + b), lda, mm, mm, b);
+                h->count(1);
+            } else if (!c.rc) {
                 c.rc = gemm_device(h, N, p, n - r0 - b, n - r0 - b, b, -1, at(c, r0 + b, r0), lda,
                                    at(c, r0, r0 + b), lda, 1, at(c, r0 + b, r0 + b), lda, opts);
+            }
         }
     }
     h->phase(-1);
@@ -880,7 +927,7 @@ int getrs_device(ozlu_handle* h, int p, int n, int nrhs, double* LU, long long l
     int rc = 0;
     auto L = [&](long long i, long long j) { return LU + (i + j * lda) * N; };
     auto X = [&](long long i) { return B + i * N; };
-    h->phase(PH_PANEL);
+    h->phase(PH_TRSM);
     h->count(1 + 3 * ((n + BASE - 1) / BASE));
     for (int r = 0; r < n && !rc; r += BASE) {
         const int b = BASE < n - r ? BASE : n - r;

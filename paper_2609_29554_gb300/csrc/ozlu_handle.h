@@ -56,7 +56,7 @@ struct ozlu_handle {
     void count(long long launches) { stats.launches += launches; }
 };
 
-enum { PH_CONVERT = 0, PH_GEMM = 1, PH_CRT = 2, PH_PANEL = 3, PH_OTHER = 4 };
+enum { PH_CONVERT = 0, PH_GEMM = 1, PH_CRT = 2, PH_PANEL = 3, PH_OTHER = 4, PH_TRSM = 5 };
 
 namespace ozlu {
 int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, const double* A,

@@ -33,7 +33,7 @@ _lib = None
 class ozlu_opts(ctypes.Structure):
     _fields_ = [("backend", ctypes.c_int), ("nslice", ctypes.c_int),
                 ("extra_groups", ctypes.c_int), ("g_ex", ctypes.c_int),
-                ("reserved", ctypes.c_int * 12)]
+                ("native", ctypes.c_int), ("reserved", ctypes.c_int * 11)]
 
 
 class ozlu_plan_info(ctypes.Structure):
@@ -49,7 +49,8 @@ class ozlu_stats(ctypes.Structure):
                 ("crt_launches", ctypes.c_longlong), ("panel_launches", ctypes.c_longlong),
                 ("launches", ctypes.c_longlong), ("gemm_ops", ctypes.c_double),
                 ("crt_bytes", ctypes.c_double), ("convert_bytes", ctypes.c_double),
-                ("last_backend", ctypes.c_int), ("pad_", ctypes.c_int)]
+                ("last_backend", ctypes.c_int), ("pad_", ctypes.c_int),
+                ("trsm_ms", ctypes.c_double)]
 
 
 _P = ctypes.c_void_p
@@ -98,10 +99,10 @@ def _check(fn, code):
         raise OzluError(fn, code)
 
 
-def make_opts(backend="int8", nslice=0, extra_groups=0, g_ex=0):
+def make_opts(backend="int8", nslice=0, extra_groups=0, g_ex=0, native=0):
     o = ozlu_opts()
     o.backend = BACKENDS[backend] if isinstance(backend, str) else int(backend)
-    o.nslice, o.extra_groups, o.g_ex = nslice, extra_groups, g_ex
+    o.nslice, o.extra_groups, o.g_ex, o.native = nslice, extra_groups, g_ex, native
     return o
 
 

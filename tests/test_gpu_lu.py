@@ -156,3 +156,21 @@ def test_getrf_host_pointers():
     np.testing.assert_array_equal(ozlu.from_colmajor(Ac, n), LU)
     np.testing.assert_array_equal(ipiv, ipiv_d)
     assert info[0] == info_d == 0
+
+
+@pytest.mark.parametrize("nc,n,nb", [(4, 90, 32), (2, 70, 16)])
+def test_native_blocked_lu(nc, n, nb):
+    # the blocked-naive comparison: same panels, trailing update in expansion arithmetic
+    h = handle()
+    A = random_expansions(n, n, nc, 700 + n, -2, 2)
+    dA = dev(A)
+    ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ozlu.ozlu_getrf(h, nc, 0, n, dA, n, ipiv, nb, info, ozlu.make_opts("int8", native=1))
+    torch.cuda.synchronize()
+    LU = host(dA, n)
+    assert int(info.item()) == 0
+    bits = _backward_error_bits(A, LU, ipiv.cpu().numpy())
+    assert bits < -53 * nc + math.log2(n) + 12, bits
+    _, LU2, ipiv2, _ = _getrf(A, nb)
+    np.testing.assert_array_equal(ipiv.cpu().numpy(), ipiv2)
