@@ -76,14 +76,20 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(v, world):
+def max_over_ranks(v, world, device="cuda"):
+    """Largest value over the ranks (the slowest rank's time)."""
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    t = torch.tensor([v], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_value(flops_per_rank, world, ms_max):
+    """Whole-job throughput: the flops of all ranks over the slowest rank's time."""
+    return flops_per_rank * world / (ms_max * 1e-3) / 1e9
 
 
 class Clocks:
@@ -346,7 +352,7 @@ def main():
     st = ozlu.ozlu_get_stats(h)
     ozlu.ozlu_set_timing(h, 0)
     ms_max = max_over_ranks(ms, world)
-    value = flops * world / (ms_max * 1e-3) / 1e9
+    value = job_value(flops, world, ms_max)
     assert int(info.item()) == 0, "singular pivot in the benchmark matrix"
 
     peaks, src = measured_peaks()
