@@ -71,7 +71,10 @@ typedef struct {
     int native;       /* ozlu_getrf only: 1 = trailing update (P4) by per-element
                          multiply-adds in expansion arithmetic, the "blocked naive"
                          comparison of Sec. 3.4 (panels unchanged)                */
-    int reserved[11];
+    int graph;        /* batched calls only: 1 = capture the batch in a CUDA graph on
+                         the second call with the same sizes and pointers and replay
+                         it from then on                                          */
+    int reserved[10];
 } ozlu_opts;
 
 /* Plan of one Ozaki-II GEMM (Sec. 3.2 "Determining w and N"). */
@@ -127,6 +130,33 @@ int ozlu_getrf(ozlu_handle* handle, int nc, int p, int n, double* A, long long l
 int ozlu_getrs(ozlu_handle* handle, int nc, int p, int n, int nrhs,
                const double* LU, long long lda, const int* ipiv,
                double* B, long long ldb, const ozlu_opts* opts);
+
+/*
+ * Batched LU of `count` independent instances of different sizes (the
+ * batched, uneven workload; each instance is the LU of Sec. 3.4).
+ *   n, A, lda, ipiv   host arrays of length count; A[i] (n[i] x n[i] expansions,
+ *                     column-major, lda[i]) and ipiv[i] (n[i] ints) are device
+ *                     pointers, factored in place as by ozlu_getrf
+ *   info              device array of count ints (LAPACK info per instance)
+ *   nb                panel width (0 = 128)
+ * Instances run on up to 8 streams owned by the handle (joined back into the
+ * handle's stream before return; the call does not wait for the GPU).  With
+ * opts->graph the batch is captured into a CUDA graph on the second call with
+ * the same sizes and pointers and replayed afterwards; the first call warms the
+ * workspaces and the back-end autotuner.
+ */
+int ozlu_getrf_batched(ozlu_handle* handle, int nc, int p, int count, const int* n,
+                       double* const* A, const long long* lda, int* const* ipiv, int* info,
+                       int nb, const ozlu_opts* opts);
+
+/*
+ * Batched solve A_i X_i = B_i from ozlu_getrf_batched's factors; B[i] is
+ * n[i] x nrhs (device, ldb[i]), overwritten by X_i.  Streams and graphs as
+ * for ozlu_getrf_batched.
+ */
+int ozlu_getrs_batched(ozlu_handle* handle, int nc, int p, int count, const int* n, int nrhs,
+                       const double* const* LU, const long long* lda, const int* const* ipiv,
+                       double* const* B, const long long* ldb, const ozlu_opts* opts);
 
 /*
  * Intermediates of the last ozlu_gemm on this handle, copied to host memory

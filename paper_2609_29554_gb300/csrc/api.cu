@@ -286,6 +286,17 @@ int ozlu_create(ozlu_handle** handle, void* stream) {
 int ozlu_destroy(ozlu_handle* h) {
     if (!h) return OZLU_OK;
     cudaStreamSynchronize(h->stream);
+    for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+    h->graphs.clear();
+    for (int k = 0; k < 8; ++k) {
+        if (h->sub[k]) {
+            cudaStream_t s = h->sub[k]->stream;
+            ozlu_destroy(h->sub[k]);
+            cudaStreamDestroy(s);
+        }
+        if (h->join[k]) cudaEventDestroy(h->join[k]);
+    }
+    if (h->fork) cudaEventDestroy(h->fork);
     h->ws.release();
     h->stage.release();
     h->tune_ws.release();

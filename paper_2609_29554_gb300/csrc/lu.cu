@@ -782,9 +782,13 @@ bool base_block_coop(double* A, long long lda, int n, int c0, int b, int p0, int
     constexpr int L = Limbs<N>::L;
     static int sms = 0;
     if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    // at least 16 rows per block: a small panel takes a few SMs and leaves the
+    // rest to concurrent work (the batched driver runs instances side by side)
+    const int g_rows = (n - c0 + 15) / 16;
     for (int per_sm = 1; per_sm <= 2; ++per_sm) {
         int G = sms * per_sm;
         if (G > COOP_MAXG) G = COOP_MAXG;
+        if (G > g_rows) G = g_rows < 1 ? 1 : g_rows;
         const int rows = (n - c0 + G - 1) / G;
         const size_t smem = sizeof(MPF<L>) * (size_t)rows * b;
         if (smem > 200 * 1024 / per_sm) continue;
@@ -795,10 +799,18 @@ bool base_block_coop(double* A, long long lda, int n, int c0, int b, int p0, int
                                                       smem);
         if (active * sms < G) continue;
         auto* sc = reinterpret_cast<CoopScratch<L>*>(scratch);
-        void* args[] = {&A, &lda, &n, &c0, &b, &p0, &p1, (void*)&rows, &ipiv, &info, &sc};
-        int rows_arg = rows;
-        args[7] = &rows_arg;
-        if (cudaLaunchCooperativeKernel((void*)base_block_coop_kernel<N>, G, COOP_THREADS, args, smem, s) !=
+        // cooperative launch (all blocks co-resident), also valid under stream capture
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(G);
+        cfg.blockDim = dim3(COOP_THREADS);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, base_block_coop_kernel<N>, A, lda, n, c0, b, p0, p1, rows, ipiv, info, sc) !=
             cudaSuccess) {
             cudaGetLastError();
             return false;
@@ -885,6 +897,8 @@ void panel_rec(Ctx& c, int r, int b, int p0, int p1) {
     panel_rec<N>(c, r + b1, b - b1, p0, p1);
 }
 
+}  // namespace
+
 template <int N>
 int getrf_device(ozlu_handle* h, int p, int n, double* A, long long lda, int* ipiv, int nb,
                  LuScratch* sc, const ozlu_opts* opts) {
@@ -948,9 +962,47 @@ int getrs_device(ozlu_handle* h, int p, int n, int nrhs, double* LU, long long l
     return rc;
 }
 
+namespace {
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
-
 }  // namespace
+
+int lu_scratch(ozlu_handle* h, LuScratch** out);
+int coop_reset(ozlu_handle* h, cudaStream_t s);
+
+// one factorisation on device pointers (the batched driver calls it per
+// instance on its own streams); info of the instance goes to *info_out
+int getrf_one(ozlu_handle* h, int nc, int p, int n, double* A, long long lda, int* ipiv, int nb, int* info_out,
+              const ozlu_opts* opts) {
+    LuScratch* sc;
+    int rc = lu_scratch(h, &sc);
+    if (rc) return rc;
+    cudaStream_t s = h->stream;
+    if (cudaMemsetAsync(sc, 0, sizeof(LuScratch), s)) return OZLU_ERR_CUDA;
+    if ((rc = coop_reset(h, s))) return rc;
+    if (n > 0) {
+        switch (nc) {
+            case 2: rc = getrf_device<2>(h, p, n, A, lda, ipiv, nb, sc, opts); break;
+            case 3: rc = getrf_device<3>(h, p, n, A, lda, ipiv, nb, sc, opts); break;
+            default: rc = getrf_device<4>(h, p, n, A, lda, ipiv, nb, sc, opts); break;
+        }
+    }
+    if (rc) return rc;
+    return cudaMemcpyAsync(info_out, &sc->info, sizeof(int), cudaMemcpyDeviceToDevice, s) == cudaSuccess
+               ? OZLU_OK
+               : OZLU_ERR_CUDA;
+}
+
+int getrs_one(ozlu_handle* h, int nc, int p, int n, int nrhs, const double* LU, long long lda, const int* ipiv,
+              double* B, long long ldb, const ozlu_opts* opts) {
+    LuScratch* sc;
+    int rc = lu_scratch(h, &sc);
+    if (rc) return rc;
+    switch (nc) {
+        case 2: return getrs_device<2>(h, p, n, nrhs, (double*)LU, lda, ipiv, B, ldb, opts, sc);
+        case 3: return getrs_device<3>(h, p, n, nrhs, (double*)LU, lda, ipiv, B, ldb, opts, sc);
+        default: return getrs_device<4>(h, p, n, nrhs, (double*)LU, lda, ipiv, B, ldb, opts, sc);
+    }
+}
 
 int lu_scratch(ozlu_handle* h, LuScratch** out) {
     if (!h->lu_scratch) {
@@ -1031,7 +1083,7 @@ extern "C" int ozlu_getrf(ozlu_handle* h, int nc, int p, int n, double* A, long 
         }
     }
     if (rc) return rc;
-    if ((rc = coop_error(h, s))) return rc;
+    if (!h->capturing && (rc = coop_error(h, s))) return rc;
     if (!dA && cudaMemcpyAsync(A, gA, abytes, cudaMemcpyDeviceToHost, s)) return OZLU_ERR_CUDA;
     if (n && gP != ipiv &&
         cudaMemcpyAsync(ipiv, gP, sizeof(int) * n, dP ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s))

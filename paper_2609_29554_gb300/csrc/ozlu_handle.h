@@ -54,11 +54,22 @@ struct ozlu_handle {
     void phase(int ph);     // close the open phase (if any) and open ph (-1: none)
     void resolve_times();
     void count(long long launches) { stats.launches += launches; }
+    bool capturing = false;  // inside a CUDA-graph capture: no host synchronisation
+    // batched driver: sub-handles with their own streams and workspaces, fork/join
+    // events, and instantiated graphs keyed by the batch description
+    ozlu_handle* sub[8] = {};
+    cudaEvent_t fork = nullptr, join[8] = {};
+    std::map<std::vector<long long>, cudaGraphExec_t> graphs;
+    std::map<std::vector<long long>, int> warm;
 };
 
 enum { PH_CONVERT = 0, PH_GEMM = 1, PH_CRT = 2, PH_PANEL = 3, PH_OTHER = 4, PH_TRSM = 5 };
 
 namespace ozlu {
+int getrf_one(ozlu_handle* h, int nc, int p, int n, double* A, long long lda, int* ipiv, int nb, int* info_out,
+              const ozlu_opts* opts);
+int getrs_one(ozlu_handle* h, int nc, int p, int n, int nrhs, const double* LU, long long lda, const int* ipiv,
+              double* B, long long ldb, const ozlu_opts* opts);
 int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, const double* A,
                 long long lda, const double* B, long long ldb, int beta, double* C,
                 long long ldc, const ozlu_opts* opts);

@@ -33,7 +33,8 @@ _lib = None
 class ozlu_opts(ctypes.Structure):
     _fields_ = [("backend", ctypes.c_int), ("nslice", ctypes.c_int),
                 ("extra_groups", ctypes.c_int), ("g_ex", ctypes.c_int),
-                ("native", ctypes.c_int), ("reserved", ctypes.c_int * 11)]
+                ("native", ctypes.c_int), ("graph", ctypes.c_int),
+                ("reserved", ctypes.c_int * 10)]
 
 
 class ozlu_plan_info(ctypes.Structure):
@@ -70,6 +71,8 @@ SIGNATURES = {
     "ozlu_set_timing": (_I, [_P, _I]),
     "ozlu_get_stats": (_I, [_P, ctypes.POINTER(ozlu_stats)]),
     "ozlu_gemm_noalloc": (_I, [_I, _I, _I, _I, _I, _I, _P, _L, _P, _L, _I, _P, _L, _P]),
+    "ozlu_getrf_batched": (_I, [_P, _I, _I, _I, _P, _P, _P, _P, _P, _I, ctypes.POINTER(ozlu_opts)]),
+    "ozlu_getrs_batched": (_I, [_P, _I, _I, _I, _P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(ozlu_opts)]),
 }
 
 
@@ -99,10 +102,10 @@ def _check(fn, code):
         raise OzluError(fn, code)
 
 
-def make_opts(backend="int8", nslice=0, extra_groups=0, g_ex=0, native=0):
+def make_opts(backend="int8", nslice=0, extra_groups=0, g_ex=0, native=0, graph=0):
     o = ozlu_opts()
     o.backend = BACKENDS[backend] if isinstance(backend, str) else int(backend)
-    o.nslice, o.extra_groups, o.g_ex, o.native = nslice, extra_groups, g_ex, native
+    o.nslice, o.extra_groups, o.g_ex, o.native, o.graph = nslice, extra_groups, g_ex, native, graph
     return o
 
 
@@ -168,6 +171,33 @@ def ozlu_gemm_noalloc(nc, p, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, strea
     _check("ozlu_gemm_noalloc", lib().ozlu_gemm_noalloc(nc, p, m, n, k, alpha, _ptr(A), lda, _ptr(B),
                                                         ldb, beta, _ptr(C), ldc,
                                                         _stream_ptr(stream)))
+
+
+def _arrays(ns, mats, lds, pivs):
+    cnt = len(ns)
+    n_arr = (ctypes.c_int * cnt)(*[int(v) for v in ns])
+    a_arr = (ctypes.c_void_p * cnt)(*[_ptr(x) for x in mats])
+    l_arr = (ctypes.c_longlong * cnt)(*[int(v) for v in lds])
+    p_arr = (ctypes.c_void_p * cnt)(*[_ptr(x) for x in pivs])
+    return n_arr, a_arr, l_arr, p_arr
+
+
+def ozlu_getrf_batched(h, nc, p, ns, mats, lds, pivs, info, nb=0, opts=None):
+    """Batched LU: ns sizes, mats/pivs device tensors, info a device int32 tensor."""
+    n_arr, a_arr, l_arr, p_arr = _arrays(ns, mats, lds, pivs)
+    _check("ozlu_getrf_batched", lib().ozlu_getrf_batched(
+        h, nc, p, len(ns), n_arr, a_arr, l_arr, p_arr, _ptr(info), nb,
+        ctypes.byref(opts) if opts else None))
+
+
+def ozlu_getrs_batched(h, nc, p, ns, nrhs, lus, lds, pivs, bs, ldbs, opts=None):
+    n_arr, a_arr, l_arr, p_arr = _arrays(ns, lus, lds, pivs)
+    cnt = len(ns)
+    b_arr = (ctypes.c_void_p * cnt)(*[_ptr(x) for x in bs])
+    lb_arr = (ctypes.c_longlong * cnt)(*[int(v) for v in ldbs])
+    _check("ozlu_getrs_batched", lib().ozlu_getrs_batched(
+        h, nc, p, cnt, n_arr, nrhs, a_arr, l_arr, p_arr, b_arr, lb_arr,
+        ctypes.byref(opts) if opts else None))
 
 
 def ozlu_debug_fetch(h, what, out: np.ndarray):
