@@ -71,9 +71,11 @@ typedef struct {
     int native;       /* ozlu_getrf only: 1 = trailing update (P4) by per-element
                          multiply-adds in expansion arithmetic, the "blocked naive"
                          comparison of Sec. 3.4 (panels unchanged)                */
-    int graph;        /* batched calls only: 1 = capture the batch in a CUDA graph on
-                         the second call with the same sizes and pointers and replay
-                         it from then on                                          */
+    int graph;        /* ozlu_getrf/ozlu_getrs (device pointers) and the batched
+                         calls: 1 = capture the call's work in a CUDA graph on the
+                         second call with the same sizes and pointers and replay it
+                         from then on (no host synchronisation inside the call; a
+                         bounded-wait timeout shows in info, see the batched LU) */
     int reserved[10];
 } ozlu_opts;
 
@@ -137,7 +139,9 @@ int ozlu_getrs(ozlu_handle* handle, int nc, int p, int n, int nrhs,
  *   n, A, lda, ipiv   host arrays of length count; A[i] (n[i] x n[i] expansions,
  *                     column-major, lda[i]) and ipiv[i] (n[i] ints) are device
  *                     pointers, factored in place as by ozlu_getrf
- *   info              device array of count ints (LAPACK info per instance)
+ *   info              device array of count ints: LAPACK info per instance (0, or
+ *                     the 1-based column of the first exactly zero pivot), or
+ *                     -OZLU_ERR_TIMEOUT when a bounded device wait gave up
  *   nb                panel width (0 = 128)
  * Instances run on up to 8 streams owned by the handle (joined back into the
  * handle's stream before return; the call does not wait for the GPU).  With
@@ -168,8 +172,8 @@ int ozlu_getrs_batched(ozlu_handle* handle, int nc, int p, int count, const int*
  *   5 t values      uint8 [gi][l][j][i] (column-major m x n per plane);
  *                   uint32 for the binary64 back-end
  *   6 device error word (int32): 0, or OZLU_ERR_TIMEOUT when a bounded
- *     wait inside a tensor-core GEMM gave up (sticky until the workspace
- *     is reallocated)
+ *     wait inside a tensor-core GEMM gave up since the start of the last
+ *     ozlu_gemm, ozlu_getrf or ozlu_getrs call on this handle
  * Residues (3, 4) are available for the INT8 back-end only.
  * bytes must be at least the size of the requested array.
  */
@@ -192,7 +196,10 @@ typedef struct {
     long long gemm_launches, crt_launches, panel_launches, launches;
     double gemm_ops, crt_bytes, convert_bytes;
     int last_backend;  /* back-end of the last residue GEMM (after autotuning) */
-    int pad_;
+    int graph_status;  /* last batched call with opts->graph: 0 ran eagerly (first
+                          call), 1 captured and launched a graph, 2 replayed one,
+                          -e capture or instantiation failed with cudaError_t e
+                          (the batch then runs eagerly on every call)        */
     double trsm_ms;
 } ozlu_stats;
 int ozlu_set_timing(ozlu_handle* handle, int enable);

@@ -21,6 +21,26 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// the handle's device error word (OZLU_ERR_TIMEOUT from a bounded wait in a
+// tensor-core GEMM); allocated once, zeroed in stream order by each call
+int* err_word(ozlu_handle* h) {
+    if (!h->dev_err) {
+        if (cudaMalloc(&h->dev_err, 256) != cudaSuccess) {
+            cudaGetLastError();
+            h->dev_err = nullptr;
+            return nullptr;
+        }
+        if (cudaMemsetAsync(h->dev_err, 0, 256, h->stream) != cudaSuccess) return nullptr;
+    }
+    return h->dev_err;
+}
+
+int clear_err_word(ozlu_handle* h) {
+    int* e = err_word(h);
+    if (!e) return OZLU_ERR_NOMEM;
+    return cudaMemsetAsync(e, 0, sizeof(int), h->stream) == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
+}
+
 int Workspace::ensure(size_t bytes) {
     if (bytes <= cap) return OZLU_OK;
     if (base) cudaFree(base);
@@ -177,8 +197,8 @@ int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, c
     L.ra = off; off = align_up(off + (size_t)pl->N * pl->S * P * Mpad * Kpad * esz);
     L.rb = off; off = align_up(off + (size_t)pl->N * pl->S * P * Npad * Kpad * esz);
     L.t = off;  off = align_up(off + (size_t)pl->G * pl->N * m * n * tsz);
-    L.err = off; off = align_up(off + sizeof(int));
-    const bool fresh = h->ws.cap < off;
+    int* derr = err_word(h);
+    if (!derr) return OZLU_ERR_NOMEM;
     rc = h->ws.ensure(off);
     if (rc) return rc;
     char* base = (char*)h->ws.base;
@@ -187,11 +207,6 @@ int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, c
     void* RA = base + L.ra;
     void* RB = base + L.rb;
     uint8_t* T = (uint8_t*)(base + L.t);
-    int* derr = (int*)(base + L.err);
-    if (fresh || h->err_off != L.err) {
-        if (cudaMemsetAsync(derr, 0, sizeof(int), s)) return OZLU_ERR_CUDA;
-        h->err_off = L.err;
-    }
     const int prev = h->open_phase;
     h->phase(PH_CONVERT);
     launch_row_shifts(A, lda, nc, m, k, pl->Q, mu, s);
@@ -286,7 +301,8 @@ int ozlu_create(ozlu_handle** handle, void* stream) {
 int ozlu_destroy(ozlu_handle* h) {
     if (!h) return OZLU_OK;
     cudaStreamSynchronize(h->stream);
-    for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+    for (auto& g : h->graphs)
+        if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
     h->graphs.clear();
     for (int k = 0; k < 8; ++k) {
         if (h->sub[k]) {
@@ -297,6 +313,8 @@ int ozlu_destroy(ozlu_handle* h) {
         if (h->join[k]) cudaEventDestroy(h->join[k]);
     }
     if (h->fork) cudaEventDestroy(h->fork);
+    if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->dev_err) cudaFree(h->dev_err);
     h->ws.release();
     h->stage.release();
     h->tune_ws.release();
@@ -315,6 +333,8 @@ int ozlu_set_stream(ozlu_handle* h, void* stream) {
 
 int ozlu_set_timing(ozlu_handle* h, int enable) {
     if (!h) return -1;
+    for (int k = 0; k < 8; ++k)
+        if (h->sub[k]) ozlu_set_timing(h->sub[k], enable);
     h->phase(-1);
     h->resolve_times();
     h->timing = enable != 0;
@@ -322,11 +342,35 @@ int ozlu_set_timing(ozlu_handle* h, int enable) {
     return OZLU_OK;
 }
 
+// the handle's counters plus those of its batched-driver sub-handles (phase
+// times of concurrent sub-streams add up, so they may exceed the wall time)
 int ozlu_get_stats(ozlu_handle* h, ozlu_stats* out) {
     if (!h) return -1;
     if (!out) return -2;
+    h->phase(-1);
     h->resolve_times();
     *out = h->stats;
+    for (int k = 0; k < 8; ++k) {
+        ozlu_handle* s = h->sub[k];
+        if (!s) continue;
+        s->phase(-1);
+        s->resolve_times();
+        const ozlu_stats& d = s->stats;
+        out->convert_ms += d.convert_ms;
+        out->gemm_ms += d.gemm_ms;
+        out->crt_ms += d.crt_ms;
+        out->panel_ms += d.panel_ms;
+        out->other_ms += d.other_ms;
+        out->trsm_ms += d.trsm_ms;
+        out->gemm_launches += d.gemm_launches;
+        out->crt_launches += d.crt_launches;
+        out->panel_launches += d.panel_launches;
+        out->launches += d.launches;
+        out->gemm_ops += d.gemm_ops;
+        out->crt_bytes += d.crt_bytes;
+        out->convert_bytes += d.convert_bytes;
+        if (d.last_backend) out->last_backend = d.last_backend;
+    }
     return OZLU_OK;
 }
 
@@ -349,6 +393,8 @@ int ozlu_gemm(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, con
     if (!C && m && n) return -13;
     if (ldc < (m > 1 ? m : 1)) return -14;
     if (cudaSetDevice(h->device) != cudaSuccess) return OZLU_ERR_CUDA;
+    int rc0 = clear_err_word(h);
+    if (rc0) return rc0;
     const bool dA = !A || is_device_ptr(A), dB = !B || is_device_ptr(B), dC = !C || is_device_ptr(C);
     if (dA && dB && dC) return gemm_device(h, nc, p, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, opts);
     // stage host operands through a second device buffer
@@ -381,16 +427,21 @@ int ozlu_debug_fetch(ozlu_handle* h, int what, void* dst, size_t bytes) {
     if (!dst) return -3;
     const GemmLayout& L = h->last;
     char* base = (char*)h->ws.base;
+    if (what == 6) {
+        if (bytes < sizeof(int)) return -4;
+        if (cudaStreamSynchronize(h->stream)) return OZLU_ERR_CUDA;
+        if (!h->dev_err) {
+            *(int*)dst = 0;
+            return OZLU_OK;
+        }
+        return cuda_rc(cudaMemcpy(dst, h->dev_err, sizeof(int), cudaMemcpyDeviceToHost));
+    }
     if (!base) return OZLU_ERR_CAPACITY;
     if (cudaStreamSynchronize(h->stream)) return OZLU_ERR_CUDA;
     if (what == 1 || what == 2) {
         const size_t need = sizeof(int) * (what == 1 ? L.m : L.n);
         if (bytes < need) return -4;
         return cuda_rc(cudaMemcpy(dst, base + (what == 1 ? L.mu : L.nu), need, cudaMemcpyDeviceToHost));
-    }
-    if (what == 6) {
-        if (bytes < sizeof(int)) return -4;
-        return cuda_rc(cudaMemcpy(dst, base + L.err, sizeof(int), cudaMemcpyDeviceToHost));
     }
     if ((what == 3 || what == 4) && L.backend != OZLU_BE_INT8) return OZLU_ERR_UNSUPPORTED;
     if (what == 3 || what == 4) {

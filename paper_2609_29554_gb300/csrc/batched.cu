@@ -55,59 +55,126 @@ std::vector<std::vector<int>> assign(int count, const int* n) {
     return lists;
 }
 
-// fork onto the sub-streams, run `work(k, list)` on each, join back
-int fork_join(ozlu_handle* h, const std::vector<std::vector<int>>& lists,
-              const std::function<int(ozlu_handle*, const std::vector<int>&)>& work) {
-    if (cudaEventRecord(h->fork, h->stream) != cudaSuccess) return OZLU_ERR_CUDA;
-    int rc = OZLU_OK;
+// fork from `root` onto the sub-streams, issue the instances round-robin
+// (one instance per stream in turn, so that a full launch queue never holds
+// one stream's work alone), then join every forked stream back into `root`
+int fork_join(ozlu_handle* h, cudaStream_t root, const std::vector<std::vector<int>>& lists,
+              const std::function<int(ozlu_handle*, int)>& work) {
+    if (cudaEventRecord(h->fork, root) != cudaSuccess) return OZLU_ERR_CUDA;
+    size_t rounds = 0;
     for (int k = 0; k < NSUB; ++k) {
         if (lists[k].empty()) continue;
         ozlu_handle* s = h->sub[k];
         if (cudaStreamWaitEvent(s->stream, h->fork, 0) != cudaSuccess) return OZLU_ERR_CUDA;
         s->capturing = h->capturing;
-        s->timing = false;
-        rc = work(s, lists[k]);
-        if (rc) break;
-        if (cudaEventRecord(h->join[k], s->stream) != cudaSuccess) return OZLU_ERR_CUDA;
-        if (cudaStreamWaitEvent(h->stream, h->join[k], 0) != cudaSuccess) return OZLU_ERR_CUDA;
+        s->timing = h->timing && !h->capturing;
+        rounds = std::max(rounds, lists[k].size());
+    }
+    int rc = OZLU_OK;
+    for (size_t r = 0; r < rounds && !rc; ++r)
+        for (int k = 0; k < NSUB && !rc; ++k)
+            if (r < lists[k].size()) rc = work(h->sub[k], lists[k][r]);
+    for (int k = 0; k < NSUB; ++k) {  // join all, also after an error (a capture needs it)
+        if (lists[k].empty()) continue;
+        ozlu_handle* s = h->sub[k];
+        s->phase(-1);
+        if (cudaEventRecord(h->join[k], s->stream) != cudaSuccess ||
+            cudaStreamWaitEvent(root, h->join[k], 0) != cudaSuccess)
+            rc = rc ? rc : OZLU_ERR_CUDA;
     }
     return rc;
 }
 
-// eager, capture or replay, keyed by the batch description
+// the work counters of the sub-handles (launches, operations, bytes)
+ozlu_stats sub_counters(ozlu_handle* h) {
+    ozlu_stats c;
+    memset(&c, 0, sizeof c);
+    for (int k = 0; k < NSUB; ++k) {
+        if (!h->sub[k]) continue;
+        const ozlu_stats& s = h->sub[k]->stats;
+        c.gemm_launches += s.gemm_launches;
+        c.crt_launches += s.crt_launches;
+        c.panel_launches += s.panel_launches;
+        c.launches += s.launches;
+        c.gemm_ops += s.gemm_ops;
+        c.crt_bytes += s.crt_bytes;
+        c.convert_bytes += s.convert_bytes;
+    }
+    return c;
+}
+
+// eager, capture or replay, keyed by the batch description; a replay adds
+// the counters the captured call recorded, so the statistics count the
+// kernels a replay runs.  The capture runs on a library-owned stream (the
+// caller's stream may be the legacy default stream, which cannot capture);
+// the graph is then launched on the caller's stream.
 int run_batched(ozlu_handle* h, const std::vector<long long>& key, bool graph,
-                const std::function<int()>& issue) {
+                const std::function<int(cudaStream_t)>& issue_on) {
+    auto issue = [&]() { return issue_on(h->stream); };
     if (!graph) return issue();
     auto g = h->graphs.find(key);
-    if (g != h->graphs.end())
-        return cudaGraphLaunch(g->second, h->stream) == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
+    if (g != h->graphs.end()) {
+        if (!g->second.exec) {  // capture failed before: stay eager
+            h->stats.graph_status = g->second.status;
+            return issue();
+        }
+        if (cudaGraphLaunch(g->second.exec, h->stream) != cudaSuccess) return OZLU_ERR_CUDA;
+        h->stats.graph_status = 2;
+        const ozlu_stats& d = g->second.work;
+        ozlu_stats& s = h->stats;
+        s.gemm_launches += d.gemm_launches;
+        s.crt_launches += d.crt_launches;
+        s.panel_launches += d.panel_launches;
+        s.launches += d.launches;
+        s.gemm_ops += d.gemm_ops;
+        s.crt_bytes += d.crt_bytes;
+        s.convert_bytes += d.convert_bytes;
+        return OZLU_OK;
+    }
     if (h->warm[key] == 0) {
         const int rc = issue();
         if (!rc) h->warm[key] = 1;
+        h->stats.graph_status = 0;
         return rc;
     }
-    cudaGraph_t gr = nullptr;
-    if (cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+    auto fail = [&](cudaError_t e) -> int {
         cudaGetLastError();
+        h->graphs[key] = {nullptr, {}, -(int)e};
+        h->stats.graph_status = -(int)e;
         return issue();
-    }
+    };
+    if (!h->cap_stream && cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(cudaErrorUnknown);
+    cudaGraph_t gr = nullptr;
+    const cudaError_t be = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed);
+    if (be != cudaSuccess) return fail(be);
+    const ozlu_stats before = sub_counters(h);
     h->capturing = true;
-    const int rc = issue();
+    const int rc = issue_on(h->cap_stream);
     h->capturing = false;
-    const cudaError_t ce = cudaStreamEndCapture(h->stream, &gr);
+    ozlu_stats work = sub_counters(h);
+    work.gemm_launches -= before.gemm_launches;
+    work.crt_launches -= before.crt_launches;
+    work.panel_launches -= before.panel_launches;
+    work.launches -= before.launches;
+    work.gemm_ops -= before.gemm_ops;
+    work.crt_bytes -= before.crt_bytes;
+    work.convert_bytes -= before.convert_bytes;
+    const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &gr);
     if (rc || ce != cudaSuccess || !gr) {
-        cudaGetLastError();
         if (gr) cudaGraphDestroy(gr);
-        return rc ? rc : issue();  // capture not possible here: run eagerly
+        if (rc) {
+            cudaGetLastError();
+            return rc;
+        }
+        return fail(ce != cudaSuccess ? ce : cudaErrorUnknown);  // not capturable: run eagerly
     }
     cudaGraphExec_t ex = nullptr;
     const cudaError_t ie = cudaGraphInstantiate(&ex, gr, 0);
     cudaGraphDestroy(gr);
-    if (ie != cudaSuccess) {
-        cudaGetLastError();
-        return issue();
-    }
-    h->graphs[key] = ex;
+    if (ie != cudaSuccess) return fail(ie);
+    h->graphs[key] = {ex, work, 1};
+    h->stats.graph_status = 1;
     return cudaGraphLaunch(ex, h->stream) == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
 }
 
@@ -153,22 +220,12 @@ extern "C" int ozlu_getrf_batched(ozlu_handle* h, int nc, int p, int count, cons
         key.push_back((long long)ipiv[i]);
     }
     const auto lists = assign(count, n);
-    auto issue = [&]() -> int {
-        return fork_join(h, lists, [&](ozlu_handle* s, const std::vector<int>& list) -> int {
-            for (int i : list) {
-                const int r = getrf_one(s, nc, p, n[i], A[i], lda[i], ipiv[i], nb, info + i, &o);
-                if (r) return r;
-                s->count(1);
-            }
-            return (int)OZLU_OK;
+    auto issue = [&](cudaStream_t root) -> int {
+        return fork_join(h, root, lists, [&](ozlu_handle* s, int i) -> int {
+            return getrf_one(s, nc, p, n[i], A[i], lda[i], ipiv[i], nb, info + i, &o);
         });
     };
-    rc = run_batched(h, key, o.graph != 0, issue);
-    long long launches = 0;
-    for (int k = 0; k < NSUB; ++k)
-        if (h->sub[k]) launches += h->sub[k]->stats.launches;
-    h->stats.launches = launches;
-    return rc;
+    return run_batched(h, key, o.graph != 0, issue);
 }
 
 extern "C" int ozlu_getrs_batched(ozlu_handle* h, int nc, int p, int count, const int* n, int nrhs,
@@ -202,14 +259,10 @@ extern "C" int ozlu_getrs_batched(ozlu_handle* h, int nc, int p, int count, cons
         key.push_back((long long)ipiv[i]);
     }
     const auto lists = assign(count, n);
-    auto issue = [&]() -> int {
-        return fork_join(h, lists, [&](ozlu_handle* s, const std::vector<int>& list) -> int {
-            for (int i : list) {
-                if (n[i] == 0) continue;
-                const int r = getrs_one(s, nc, p, n[i], nrhs, LU[i], lda[i], ipiv[i], B[i], ldb[i], &o);
-                if (r) return r;
-            }
-            return (int)OZLU_OK;
+    auto issue = [&](cudaStream_t root) -> int {
+        return fork_join(h, root, lists, [&](ozlu_handle* s, int i) -> int {
+            if (n[i] == 0) return (int)OZLU_OK;
+            return getrs_one(s, nc, p, n[i], nrhs, LU[i], lda[i], ipiv[i], B[i], ldb[i], &o);
         });
     };
     return run_batched(h, key, o.graph != 0, issue);

@@ -45,6 +45,7 @@ struct LuScratch {
     int zero;
     unsigned int counter;
     int info;
+    int result;                 // info as reported by ozlu_getrf (finish_kernel)
     double pval[MAXPART][4];    // block candidates (expansion values)
     int pidx[MAXPART];
     int plist[1 + 4 * LMAXB];   // interchange permutation: count, (dst, src) pairs
@@ -780,8 +781,9 @@ template <int N>
 bool base_block_coop(double* A, long long lda, int n, int c0, int b, int p0, int p1, int* ipiv,
                      int* info, void* scratch, cudaStream_t s) {
     constexpr int L = Limbs<N>::L;
-    static int sms = 0;
-    if (!sms) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // at least 16 rows per block: a small panel takes a few SMs and leaves the
     // rest to concurrent work (the batched driver runs instances side by side)
     const int g_rows = (n - c0 + 15) / 16;
@@ -969,6 +971,18 @@ size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 int lu_scratch(ozlu_handle* h, LuScratch** out);
 int coop_reset(ozlu_handle* h, cudaStream_t s);
 
+namespace {
+// info of one factorisation: the first zero pivot (1-based), or
+// -OZLU_ERR_TIMEOUT when a bounded wait of the panel kernel (its error word)
+// or of a tensor-core GEMM (the handle's error word) gave up
+__global__ void finish_kernel(int* info_out, const LuScratch* sc, const int* coop, const int* gerr) {
+    int v = sc->info;
+    if (coop[2]) v = -coop[2];
+    else if (*gerr) v = -*gerr;
+    *info_out = v;
+}
+}  // namespace
+
 // one factorisation on device pointers (the batched driver calls it per
 // instance on its own streams); info of the instance goes to *info_out
 int getrf_one(ozlu_handle* h, int nc, int p, int n, double* A, long long lda, int* ipiv, int nb, int* info_out,
@@ -979,6 +993,7 @@ int getrf_one(ozlu_handle* h, int nc, int p, int n, double* A, long long lda, in
     cudaStream_t s = h->stream;
     if (cudaMemsetAsync(sc, 0, sizeof(LuScratch), s)) return OZLU_ERR_CUDA;
     if ((rc = coop_reset(h, s))) return rc;
+    if ((rc = clear_err_word(h))) return rc;
     if (n > 0) {
         switch (nc) {
             case 2: rc = getrf_device<2>(h, p, n, A, lda, ipiv, nb, sc, opts); break;
@@ -987,9 +1002,9 @@ int getrf_one(ozlu_handle* h, int nc, int p, int n, double* A, long long lda, in
         }
     }
     if (rc) return rc;
-    return cudaMemcpyAsync(info_out, &sc->info, sizeof(int), cudaMemcpyDeviceToDevice, s) == cudaSuccess
-               ? OZLU_OK
-               : OZLU_ERR_CUDA;
+    finish_kernel<<<1, 1, 0, s>>>(info_out, sc, (const int*)h->coop_scratch, h->dev_err);
+    h->count(1);
+    return cudaGetLastError() == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
 }
 
 int getrs_one(ozlu_handle* h, int nc, int p, int n, int nrhs, const double* LU, long long lda, const int* ipiv,
@@ -997,6 +1012,7 @@ int getrs_one(ozlu_handle* h, int nc, int p, int n, int nrhs, const double* LU, 
     LuScratch* sc;
     int rc = lu_scratch(h, &sc);
     if (rc) return rc;
+    if ((rc = clear_err_word(h))) return rc;
     switch (nc) {
         case 2: return getrs_device<2>(h, p, n, nrhs, (double*)LU, lda, ipiv, B, ldb, opts, sc);
         case 3: return getrs_device<3>(h, p, n, nrhs, (double*)LU, lda, ipiv, B, ldb, opts, sc);
@@ -1029,13 +1045,13 @@ int coop_reset(ozlu_handle* h, cudaStream_t s) {
                                                                                    : OZLU_ERR_CUDA;
 }
 
-int coop_error(ozlu_handle* h, cudaStream_t s) {
-    int err = 0;
-    if (cudaMemcpyAsync(&err, (char*)h->coop_scratch + 2 * sizeof(int), sizeof(int),
-                        cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+// waits for the stream; OZLU_ERR_TIMEOUT if a bounded device wait gave up
+int lu_result(ozlu_handle* h, cudaStream_t s, int* result) {
+    LuScratch* sc = (LuScratch*)h->lu_scratch;
+    if (cudaMemcpyAsync(result, &sc->result, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return OZLU_ERR_CUDA;
-    return err;
+    return *result < 0 ? -*result : OZLU_OK;
 }
 
 }  // namespace ozlu
@@ -1060,9 +1076,9 @@ extern "C" int ozlu_getrf(ozlu_handle* h, int nc, int p, int n, double* A, long 
     LuScratch* sc;
     int rc = lu_scratch(h, &sc);
     if (rc) return rc;
-    if (cudaMemsetAsync(sc, 0, sizeof(LuScratch), s)) return OZLU_ERR_CUDA;
-    if ((rc = coop_reset(h, s))) return rc;
     const bool dA = is_device_ptr(A), dP = is_device_ptr(ipiv), dI = is_device_ptr(info);
+    if (opts && opts->graph && n > 0 && dA && dP && dI)  // graph capture and replay
+        return ozlu_getrf_batched(h, nc, p, 1, &n, &A, &lda, &ipiv, info, nb, opts);
     const size_t abytes = sizeof(double) * nc * (size_t)lda * (n ? n : 1);
     double* gA = A;
     int* gP = ipiv;
@@ -1075,15 +1091,9 @@ extern "C" int ozlu_getrf(ozlu_handle* h, int nc, int p, int n, double* A, long 
         }
         if (!dP) gP = (int*)((char*)h->stage.base + align256(abytes));
     }
-    if (n > 0) {
-        switch (nc) {
-            case 2: rc = getrf_device<2>(h, p, n, gA, lda, gP, nb, sc, opts); break;
-            case 3: rc = getrf_device<3>(h, p, n, gA, lda, gP, nb, sc, opts); break;
-            default: rc = getrf_device<4>(h, p, n, gA, lda, gP, nb, sc, opts); break;
-        }
-    }
-    if (rc) return rc;
-    if (!h->capturing && (rc = coop_error(h, s))) return rc;
+    if ((rc = getrf_one(h, nc, p, n, gA, lda, gP, nb, &sc->result, opts))) return rc;
+    int result = 0;
+    if ((rc = lu_result(h, s, &result))) return rc;
     if (!dA && cudaMemcpyAsync(A, gA, abytes, cudaMemcpyDeviceToHost, s)) return OZLU_ERR_CUDA;
     if (n && gP != ipiv &&
         cudaMemcpyAsync(ipiv, gP, sizeof(int) * n, dP ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s))
@@ -1114,7 +1124,10 @@ extern "C" int ozlu_getrs(ozlu_handle* h, int nc, int p, int n, int nrhs, const 
     LuScratch* sc;
     int rc0 = lu_scratch(h, &sc);
     if (rc0) return rc0;
+    if ((rc0 = clear_err_word(h))) return rc0;
     const bool dL = is_device_ptr(LU), dP = is_device_ptr(ipiv), dB = is_device_ptr(B);
+    if (opts && opts->graph && dL && dP && dB)  // graph capture and replay
+        return ozlu_getrs_batched(h, nc, p, 1, &n, nrhs, &LU, &lda, &ipiv, &B, &ldb, opts);
     const size_t lbytes = sizeof(double) * nc * (size_t)lda * n;
     const size_t bbytes = sizeof(double) * nc * (size_t)ldb * nrhs;
     const double* gL = LU;

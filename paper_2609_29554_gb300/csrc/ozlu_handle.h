@@ -25,7 +25,7 @@ struct PlanEntry {
 // byte offsets of the last ozlu_gemm's intermediates inside the workspace
 struct GemmLayout {
     int m = 0, n = 0, k = 0, Mpad = 0, Npad = 0, Kpad = 0, N = 0, S = 0, G = 0, backend = 0;
-    size_t mu = 0, nu = 0, ra = 0, rb = 0, t = 0, err = 0;
+    size_t mu = 0, nu = 0, ra = 0, rb = 0, t = 0;
 };
 
 }  // namespace ozlu
@@ -39,7 +39,7 @@ struct ozlu_handle {
     std::map<std::tuple<int, int, int, int, int, int>, int> tuned;  // shape key -> back-end
     std::map<std::tuple<int, int, int, int, int, int>, ozlu::PlanEntry> plans;
     ozlu::GemmLayout last;
-    size_t err_off = (size_t)-1;  // workspace offset of the device error word
+    int* dev_err = nullptr;  // device error word of the tensor-core GEMMs
     bool timing = false;
     ozlu_stats stats = {};
     void* lu_scratch = nullptr;  // pivot-search scratch of ozlu_getrf
@@ -58,8 +58,14 @@ struct ozlu_handle {
     // batched driver: sub-handles with their own streams and workspaces, fork/join
     // events, and instantiated graphs keyed by the batch description
     ozlu_handle* sub[8] = {};
+    cudaStream_t cap_stream = nullptr;  // graph captures run here
     cudaEvent_t fork = nullptr, join[8] = {};
-    std::map<std::vector<long long>, cudaGraphExec_t> graphs;
+    struct Graph {
+        cudaGraphExec_t exec;  // null: capture failed, the batch runs eagerly
+        ozlu_stats work;       // counters of the captured call, added on each replay
+        int status;            // graph_status of ozlu_stats
+    };
+    std::map<std::vector<long long>, Graph> graphs;
     std::map<std::vector<long long>, int> warm;
 };
 
@@ -74,5 +80,7 @@ int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, c
                 long long lda, const double* B, long long ldb, int beta, double* C,
                 long long ldc, const ozlu_opts* opts);
 bool is_device_ptr(const void* p);
+int* err_word(ozlu_handle* h);
+int clear_err_word(ozlu_handle* h);
 int cuda_rc(cudaError_t e);
 }  // namespace ozlu

@@ -50,7 +50,7 @@ class ozlu_stats(ctypes.Structure):
                 ("crt_launches", ctypes.c_longlong), ("panel_launches", ctypes.c_longlong),
                 ("launches", ctypes.c_longlong), ("gemm_ops", ctypes.c_double),
                 ("crt_bytes", ctypes.c_double), ("convert_bytes", ctypes.c_double),
-                ("last_backend", ctypes.c_int), ("pad_", ctypes.c_int),
+                ("last_backend", ctypes.c_int), ("graph_status", ctypes.c_int),
                 ("trsm_ms", ctypes.c_double)]
 
 

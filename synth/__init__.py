@@ -16,10 +16,12 @@ arguments (numpy default_rng seeds).
                       A = U diag(sigma) V^T with U, V from the QR of seeded
                       N(0, 1) matrices and sigma geometric from 1 to 10^-c,
                       formed exactly (synth/prescribed.py)
+  exact_row_sums      b = A * ones of a stored expansion matrix, exactly,
+                      then rounded
 """
 from .matrices import (lotkin_expansions, lotkin_rhs, random_expansions,
                        rational_to_expansion)
-from .prescribed import prescribed_cond_expansions
+from .prescribed import exact_row_sums, prescribed_cond_expansions
 
 __all__ = ["random_expansions", "lotkin_expansions", "lotkin_rhs",
-           "rational_to_expansion", "prescribed_cond_expansions"]
+           "rational_to_expansion", "prescribed_cond_expansions", "exact_row_sums"]

@@ -58,6 +58,23 @@ def _groups(e: np.ndarray):
     return groups
 
 
+def _pow2(e):
+    """Exact 2^e as float64 from its bit pattern (e an int64 tensor in [-1022, 1023]).
+
+    torch.ldexp multiplies by pow(2, e), which a device math library need not
+    return exactly; a power of two built from its exponent field always is.
+    """
+    import torch
+    return ((e + 1023) << 52).view(torch.float64)
+
+
+def _scale2(x, e):
+    """x * 2^e exactly (results in the normal range), e an int64 tensor."""
+    import torch
+    e1 = e.clamp(-1000, 1000)
+    return x * _pow2(e1) * _pow2(e - e1)
+
+
 def _carry(L):
     import torch
     for q in range(L.shape[0] - 1):
@@ -77,9 +94,14 @@ def prescribed_cond_expansions(n: int, log10_cond: float, seed: int, nc: int,
     emin = min(g for g, _ in groups)
     nlimbs = (53 + (max(g for g, _ in groups) - emin) + 8) // LIMB + 3
     L = torch.zeros((nlimbs, n, n), dtype=torch.int64, device=device)
+    # torch's CPU matmul (not numpy's BLAS, whose spinning threads would
+    # fight torch's between calls): every partial sum is an integer below
+    # 2^53, so the product is exact in any summation order
+    Ut = torch.from_numpy(Ui * m[None, :])
+    Vt = torch.from_numpy(Vi)
     for g, idx in groups:
-        T = (Ui[:, idx] * m[idx]) @ Vi[:, idx].T          # exact integers
-        t = torch.from_numpy(T.astype(np.int64)).to(device)
+        ix = torch.from_numpy(np.asarray(idx))
+        t = (Ut[:, ix] @ Vt[:, ix].T).to(torch.int64).to(device)   # exact integers
         s = g - emin
         q, r = divmod(s, LIMB)
         parts = [t & MASK, (t >> LIMB) & MASK, t >> (2 * LIMB)]
@@ -132,8 +154,7 @@ def _round_limbs(L, neg, scale_exp: int, nc: int):
         sticky = (lower_any | part_any) & (shift > 0)
         W = W | sticky.to(torch.int64)
         x = W.to(torch.float64)                           # round to nearest even
-        out[..., c] = torch.where(any_nz, sign * torch.ldexp(x, (shift + scale_exp).to(torch.float64)),
-                                  torch.zeros_like(x))
+        out[..., c] = torch.where(any_nz, sign * _scale2(x, shift + scale_exp), torch.zeros_like(x))
         # subtract the rounded value: R = int(x) (<= 2^62) placed at bit `shift`
         R = torch.where(any_nz, x.to(torch.int64), torch.zeros_like(W))
         pieces = [R & MASK, (R >> LIMB) & MASK, R >> (2 * LIMB)]
@@ -146,3 +167,48 @@ def _round_limbs(L, neg, scale_exp: int, nc: int):
         L = _carry(L)
         sign = torch.where(flip, -sign, sign)
     return out
+
+
+def exact_row_sums(A, nc: int):
+    """b_i = sum_j A_ij of an expansion matrix, exactly, rounded to nc components.
+
+    A is a (rows, cols, nc_in) float64 torch tensor with A[i, j] the
+    components of element (i, j).  Every component is an integer mantissa
+    M (|M| < 2^53) times 2^E; all of them are accumulated exactly in 24-bit
+    integer limbs relative to the smallest E, and the sum is rounded into
+    nc binary64 components by successive round-to-nearest-even.  Used for
+    right-hand sides b = A * ones of the stored (already rounded) matrix.
+    """
+    import torch
+
+    rows = A.shape[0]
+    v = A.reshape(rows, -1)
+    mant, ex = torch.frexp(v)
+    M = (mant * 2.0 ** 53).to(torch.int64)                    # exact: |M| < 2^53
+    nz = M != 0
+    out = torch.zeros((rows, nc), dtype=torch.float64, device=A.device)
+    if not bool(nz.any()):
+        return out
+    E = ex.to(torch.int64) - 53
+    emin = int(E[nz].min())
+    pos = torch.where(nz, E - emin, torch.zeros_like(E))
+    q = torch.div(pos, LIMB, rounding_mode="floor")
+    r = pos - q * LIMB
+    # three pieces of |M| (< 2^53) shifted by r < 24: each below 2^48, and a
+    # component adds at most one piece to a limb; chunks of 2^13 components
+    # keep every limb below 2^62 between carries
+    nl = int(q.max()) + 6
+    L = torch.zeros((nl, rows), dtype=torch.int64, device=A.device)
+    chunk = 1 << 13
+    for c0 in range(0, M.shape[1], chunk):
+        Mc, qc, rc = M[:, c0:c0 + chunk], q[:, c0:c0 + chunk], r[:, c0:c0 + chunk]
+        sgn = torch.sign(Mc)
+        aM = Mc.abs()
+        ridx = torch.arange(rows, device=A.device).view(rows, 1).expand_as(Mc)
+        for j, pc in enumerate((aM & MASK, (aM >> LIMB) & MASK, aM >> (2 * LIMB))):
+            L.index_put_((qc + j, ridx), sgn * (pc << rc), accumulate=True)
+        L = _carry(L)
+    neg = L[-1] < 0
+    L = torch.where(neg.unsqueeze(0), -L, L)
+    L = _carry(L)
+    return _round_limbs(L, neg, emin, nc)

@@ -45,6 +45,7 @@ def test_batched_equals_single(graph):
                 x.copy_(y)
             ozlu.ozlu_getrf_batched(h, nc, 0, SIZES, dA, SIZES, piv, info, nb, opts)
             torch.cuda.synchronize()
+            assert ozlu.ozlu_get_stats(h).graph_status == ([0, 1, 2][rep] if graph else 0)
             assert info.cpu().tolist() == [0] * len(SIZES)
             for i, n in enumerate(SIZES):
                 np.testing.assert_array_equal(host(dA[i], n), ref[i][2])
@@ -61,5 +62,39 @@ def test_batched_equals_single(graph):
         torch.cuda.synchronize()
         for b, b1 in zip(bs, bs1):
             np.testing.assert_array_equal(b.cpu().numpy(), b1.cpu().numpy())
+    finally:
+        ozlu.ozlu_destroy(h)
+
+
+def test_single_instance_graph_replay():
+    """ozlu_getrf / ozlu_getrs with opts.graph: capture on the second call, replay
+    after; the same bits as the eager calls, on the caller's (default) stream."""
+    nc, n, nb = 4, 200, 64
+    A0 = random_expansions(n, n, nc, 77, -1, 1)
+    ref = _single(A0, nc, nb, ozlu.make_opts("int8"))
+    b0 = np.ascontiguousarray(random_expansions(n, 1, nc, 78)[None, :, 0, :])
+    hs = handle()
+    xb = torch.from_numpy(b0).cuda()
+    ozlu.ozlu_getrs(hs, nc, 0, n, 1, ref[0], n, ref[1], xb, n, ozlu.make_opts("int8"))
+    torch.cuda.synchronize()
+    h = ozlu.ozlu_create(None)
+    try:
+        opts = ozlu.make_opts("int8", graph=1)
+        dA0 = dev(A0)
+        dA = dA0.clone()
+        piv = torch.zeros(n, dtype=torch.int32, device="cuda")
+        info = torch.full((1,), -7, dtype=torch.int32, device="cuda")
+        x = torch.empty_like(xb)
+        for rep in range(4):
+            dA.copy_(dA0)
+            ozlu.ozlu_getrf(h, nc, 0, n, dA, n, piv, nb, info, opts)
+            x.copy_(torch.from_numpy(b0))
+            ozlu.ozlu_getrs(h, nc, 0, n, 1, dA, n, piv, x, n, opts)
+            torch.cuda.synchronize()
+            assert ozlu.ozlu_get_stats(h).graph_status == min(rep, 2)
+            assert int(info.item()) == 0
+            np.testing.assert_array_equal(host(dA, n), ref[2])
+            np.testing.assert_array_equal(piv.cpu().numpy(), ref[3])
+            np.testing.assert_array_equal(x.cpu().numpy(), xb.cpu().numpy())
     finally:
         ozlu.ozlu_destroy(h)

@@ -47,3 +47,30 @@ def test_prescribed_cond_spectrum():
     A = prescribed_cond_expansions(n, c, 7, 2).numpy()
     s = np.linalg.svd(A[..., 0], compute_uv=False)
     assert abs(np.log10(s[0] / s[-1]) - c) < 0.1
+
+
+@pytest.mark.parametrize("nc_in,nc,seed", [(3, 3, 1), (4, 2, 2), (2, 4, 3)])
+def test_exact_row_sums(nc_in, nc, seed):
+    from synth import exact_row_sums
+    A = random_expansions(6, 11, nc_in, seed, -60, 60)
+    A[2] = 0.0                                # an all-zero row
+    A[3, :, :] = -A[4, :, :]                  # two rows that cancel each other ...
+    A[3, 0, :] = A[4, 0, :]                   # ... but for one element
+    A[5, 3, nc_in - 1] = 5e-324               # a subnormal component
+    got = exact_row_sums(torch.from_numpy(A), nc).numpy()
+    for i in range(6):
+        s = sum((Fraction(float(x)) for x in A[i].ravel()), Fraction(0))
+        k = s.denominator.bit_length() - 1
+        assert s.denominator == 1 << k
+        assert list(got[i]) == fl_expansion(s.numerator, -k, nc)
+
+
+def test_exact_row_sums_long_rows():
+    """More components per row than one accumulation chunk holds."""
+    from synth import exact_row_sums
+    A = random_expansions(2, 3000, 4, 9, -3, 3)          # 12000 components per row
+    got = exact_row_sums(torch.from_numpy(A), 2).numpy()
+    for i in range(2):
+        s = sum((Fraction(float(x)) for x in A[i].ravel()), Fraction(0))
+        k = s.denominator.bit_length() - 1
+        assert list(got[i]) == fl_expansion(s.numerator, -k, 2)
