@@ -319,60 +319,73 @@ __global__ void __launch_bounds__(128) column_step_kernel(double* A, long long l
 // ---------------------------------------------------------------------------
 // Cooperative factorisation of one base block: columns [c0, c0 + b) over rows
 // [c0, n).  One block per SM owns a contiguous slice of rows and keeps its
-// b-column slice in shared memory as L-limb floats for the whole block, so a
-// column step costs one grid barrier: each block publishes its best candidate
-// row for the next column (value, index and the whole row), every block
-// reduces the same partials to the pivot, takes the pivot row from the
-// winner's slot, applies the interchange to its rows, scales and updates.
-// The grid barrier spins with an iteration limit; on expiry the kernel records
-// OZLU_ERR_TIMEOUT in the scratch and returns.
+// b-column slice in shared memory as L-limb floats for the whole block.  A
+// column step needs one exchange: each block publishes its best candidate row
+// for the column (its index, its reciprocal and the whole row) in its slot,
+// then one 64-bit word holding the column number and an ordering key of the
+// candidate; every block waits for all G stamp words (one load each when they
+// are there), reduces the same keys to the same pivot, takes the pivot row
+// from the winner's slot, swaps it into place among its rows, scales and
+// updates.  Waiting on the stamps replaces a grid barrier, and the
+// slots are double-buffered by column parity: a block can only stamp column
+// kc + 2 after every block has stamped kc + 1, i.e. after every block has
+// finished reading the slots of column kc.  The interchanges of the columns
+// outside the base block are applied once, after the last column.
+// Every wait is bounded (2 s of the global timer); on expiry the kernel
+// records OZLU_ERR_TIMEOUT in the scratch and every block returns.
 constexpr int COOP_MAXG = 304;           // blocks (up to 2 per SM)
-constexpr int COOP_THREADS = 256;
-constexpr long long BARRIER_SPIN_LIMIT = 40000000;  // about 2 s with 32 ns naps
+constexpr int COOP_THREADS = 512;
+constexpr unsigned long long COOP_WAIT_NS = 2000000000ull;
+
+// stamp word of a slot: bits 63..44 the column (c0 + kc + 1, modulo 2^20),
+// bits 43..0 the candidate's key (mpf_key; 0: no candidate).  One 64-bit
+// store publishes both, after the rest of the slot.
+constexpr int STAMP_SHIFT = 44;
+constexpr unsigned long long KEY_MASK = (1ull << STAMP_SHIFT) - 1;
 
 template <int L>
 struct CoopSlot {
-    MPF<L> row[BASE];   // candidate row (all b columns)
-    MPF<L> rec;         // 1 / its entry in the pivot column (0 for a zero candidate)
-    int idx;            // its global row index, -1 if none
+    unsigned long long stamp;
+    int idx;                 // the candidate's global row index, -1 if none
+    int pad;
+    MPF<L> rec;              // 1 / the candidate (0 for a zero candidate)
+    MPF<L> row[BASE];        // the candidate row (all b columns)
 };
 
 template <int L>
 struct CoopScratch {
-    unsigned int bar_count;
-    unsigned int bar_gen;
     int error;
-    int pad;
+    int pad[3];
     CoopSlot<L> part[2][COOP_MAXG];  // double-buffered by column parity
     MPF<L> orow[2][BASE];            // old row c, for the owner of the pivot row
 };
 
-template <int L>
-__device__ __forceinline__ bool grid_barrier(CoopScratch<L>* sc) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        volatile unsigned int* genp = &sc->bar_gen;
-        const unsigned int gen = *genp;
-        __threadfence();
-        const unsigned int arrived = atomicAdd(&sc->bar_count, 1u) + 1u;
-        if (arrived == gridDim.x) {
-            sc->bar_count = 0;
-            __threadfence();
-            atomicAdd(&sc->bar_gen, 1u);
-        } else {
-            long long spins = 0;
-            while (*genp == gen) {
-                if (++spins > BARRIER_SPIN_LIMIT) {
-                    atomicExch(&sc->error, OZLU_ERR_TIMEOUT);
-                    break;
-                }
-                __nanosleep(32);
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
+    return *reinterpret_cast<const volatile unsigned long long*>(p);
+}
+
+// wait until the stamp word carries column `want`; returns it, or 0 on
+// expiry (the error word is then set) or when another block has given up
+__device__ __forceinline__ unsigned long long wait_stamp(const unsigned long long* p, unsigned want,
+                                                         int* err) {
+    const unsigned long long t0 = global_ns();
+    for (int it = 1;; ++it) {
+        const unsigned long long v = ld_volatile(p);
+        if ((unsigned)(v >> STAMP_SHIFT) == want) return v;
+        if ((it & 63) == 0) {
+            if (*(volatile int*)err) return 0;
+            if (global_ns() - t0 > COOP_WAIT_NS) {
+                atomicExch(err, OZLU_ERR_TIMEOUT);
+                return 0;
             }
         }
-        __threadfence();
     }
-    __syncthreads();
-    return *(volatile int*)&sc->error == 0;
 }
 
 // load an L-limb float written by another block (bypassing L1)
@@ -385,6 +398,19 @@ __device__ __forceinline__ MPF<L> ld_cg(const MPF<L>* p) {
     v.e = __ldcg(reinterpret_cast<const int*>(w + L));
     v.neg = __ldcg(reinterpret_cast<const int*>(w + L + 1));
     return v;
+}
+
+// 44-bit order key of |v|: exponent (12 bits), then the top limb (values are
+// normalised); a larger key means a larger |v|, equal keys need the full
+// comparison.  An exact zero gets 1 (below every nonzero value, above "no
+// candidate" = 0).  Exponents outside [-2047, 2047] share the lowest or the
+// highest nonzero key, so that they always go through the full comparison.
+template <int L>
+__device__ __forceinline__ unsigned long long mpf_key(const MPF<L>& v) {
+    if (mpf_zero<L>(v)) return 1ull;
+    if (v.e < -2047) return 1ull << 32;
+    if (v.e > 2047) return KEY_MASK;
+    return ((unsigned long long)(unsigned)(v.e + 2048) << 32) | v.m[L - 1];
 }
 
 // |a| > |b|, or equal and ia < ib (first index on ties); ib < 0: b is empty
@@ -412,95 +438,179 @@ __device__ __forceinline__ void warp_best(MPF<L>& v, int& idx, int& aux) {
     }
 }
 
+// warp-wide max of (key, then lowest index); idx < 0: none
+__device__ __forceinline__ void warp_best_key(unsigned long long& k, int& idx, int& aux) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long k2 = __shfl_xor_sync(0xffffffffu, k, o);
+        const int i2 = __shfl_xor_sync(0xffffffffu, idx, o);
+        const int a2 = __shfl_xor_sync(0xffffffffu, aux, o);
+        if (i2 >= 0 && (idx < 0 || k2 > k || (k2 == k && i2 < idx))) { k = k2; idx = i2; aux = a2; }
+    }
+}
+
 template <int N>
 __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
     double* A, long long lda, int n, int c0, int b, int p0, int p1, int rows_per_block,
     int* ipiv, int* info, CoopScratch<Limbs<N>::L>* sc) {
     constexpr int L = Limbs<N>::L;
+    constexpr int T = COOP_THREADS;
     extern __shared__ __align__(16) unsigned char smraw[];
     MPF<L>* a = reinterpret_cast<MPF<L>*>(smraw);  // [r][k], r < rows_per_block, k < b
-    __shared__ MPF<L> prow[BASE];
-    __shared__ MPF<L> rec;
-    __shared__ MPF<L> crec;  // reciprocal of this block's next candidate
-    __shared__ int s_piv, s_widx;
-    __shared__ MPF<L> cv[1];
-    __shared__ int ci[1];
+    // rows padded to b + 1 entries: threads on consecutive rows of one column
+    // then fall on different shared-memory banks
+    const int bs = b + 1;
+    __shared__ MPF<L> prow[BASE];  // the pivot row
+    __shared__ MPF<L> otmp[BASE];  // old row c (for the owner of the pivot row)
+    __shared__ MPF<L> rec;         // 1 / pivot
+    __shared__ MPF<L> crec;        // 1 / this block's next candidate
+    __shared__ MPF<L> cv;          // this block's next candidate
+    __shared__ int ci, s_piv, s_widx, s_fail;
+    __shared__ int s_pivs[BASE];
     const int g = blockIdx.x, G = gridDim.x, tid = threadIdx.x;
     const int r0 = c0 + g * rows_per_block;
     const int r1 = min(n, r0 + rows_per_block);
     const int nr = max(0, r1 - r0);
     auto owner = [&](int row) { return (row - c0) / rows_per_block; };
 
-    for (int p = tid; p < nr * b; p += COOP_THREADS) {
+    for (int p = tid; p < nr * b; p += T) {
         const int r = p / b, k = p - r * b;
-        a[r * b + k] = mpf_from_exp<L, N>(elem(A, lda, N, r0 + r, c0 + k));
+        a[r * bs + k] = mpf_from_exp<L, N>(elem(A, lda, N, r0 + r, c0 + k));
     }
     __syncthreads();
 
-    // this block's best candidate (largest |a|, lowest row on ties) in local
-    // column kc among rows >= row_lo; result in cv[0], ci[0]
-    // (warp 0 only; the result is in cv[0], ci[0] after the caller's barrier)
+    // warp 0: this block's best candidate in local column kc among rows >=
+    // row_lo (cv, ci) and its reciprocal (crec)
     auto candidate = [&](int kc, int row_lo) {
-        MPF<L> best = mpf_make_zero<L>();
+        unsigned long long bk = 0;
         int bi = -1, aux = 0;
         for (int r = tid; r < nr; r += 32) {
             const int i = r0 + r;
             if (i < row_lo) continue;
-            if (mpf_better<L>(a[r * b + kc], i, best, bi)) { best = a[r * b + kc]; bi = i; }
+            const unsigned long long k = mpf_key<L>(a[r * bs + kc]);
+            if (bi < 0 || k > bk ||
+                (k == bk && mpf_abs_cmp<L>(a[r * bs + kc], a[(bi - r0) * bs + kc]) > 0)) {
+                bk = k;
+                bi = i;
+            }
         }
-        warp_best<L>(best, bi, aux);
+        unsigned long long K = bk;
+        int I = bi;
+        warp_best_key(K, I, aux);
+        if (__any_sync(0xffffffffu, bi >= 0 && bk == K && bi != I)) {  // equal keys: compare exactly
+            MPF<L> v = (bi >= 0 && bk == K) ? a[(bi - r0) * bs + kc] : mpf_make_zero<L>();
+            int vi = (bi >= 0 && bk == K) ? bi : -1;
+            warp_best<L>(v, vi, aux);
+            I = vi;
+        }
         if (tid == 0) {
-            cv[0] = best;
-            ci[0] = bi;
+            ci = I;
+            cv = I >= 0 ? a[(I - r0) * bs + kc] : mpf_make_zero<L>();
+            crec = (I >= 0 && !mpf_zero<L>(cv)) ? mpf_recip<L>(cv) : mpf_make_zero<L>();
         }
     };
-    // publish the candidate row (after every column of it is final) and its reciprocal
+    // all threads: publish the candidate of column kc (every column of its row
+    // final) and, from the owner of row c0 + kc, that row's old contents
     auto publish = [&](int kc) {
         CoopSlot<L>& slot = sc->part[kc & 1][g];
-        const int wi = ci[0];
+        const int wi = ci;
+        const int c = c0 + kc;
+        if (wi >= 0)
+            for (int k = tid; k < b; k += T) slot.row[k] = a[(wi - r0) * bs + k];
+        if (owner(c) == g)
+            for (int k = tid; k < b; k += T) sc->orow[kc & 1][k] = a[(c - r0) * bs + k];
         if (tid == 0) {
             slot.idx = wi;
             slot.rec = crec;
         }
-        if (wi >= 0)
-            for (int k = tid; k < b; k += COOP_THREADS) slot.row[k] = a[(wi - r0) * b + k];
         __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            const unsigned long long key = wi >= 0 ? mpf_key<L>(cv) : 0ull;
+            *reinterpret_cast<volatile unsigned long long*>(&slot.stamp) =
+                ((unsigned long long)((c + 1) & 0xfffff) << STAMP_SHIFT) | key;
+        }
     };
 
     if (tid < 32) candidate(0, c0);
-    if (tid == 0) crec = (ci[0] >= 0 && !mpf_zero<L>(cv[0])) ? mpf_recip<L>(cv[0]) : mpf_make_zero<L>();
     __syncthreads();
     publish(0);
     for (int kc = 0; kc < b; ++kc) {
         const int c = c0 + kc;
-        // the owner of row c leaves its old contents for the pivot row's owner
-        if (owner(c) == g)
-            for (int k = tid; k < b; k += COOP_THREADS) sc->orow[kc & 1][k] = a[(c - r0) * b + k];
-        if (!grid_barrier<L>(sc)) return;
-        // every block reduces the same partials to the same pivot
+        // warp 0: wait for every stamp of column kc, reduce the keys to the pivot
         if (tid < 32) {
-            MPF<L> best = mpf_make_zero<L>();
-            int bi = -1, bw = -1;
-            for (int q = tid; q < G; q += 32) {
-                const CoopSlot<L>& slot = sc->part[kc & 1][q];
-                const int iv = __ldcg(&slot.idx);
-                if (iv < 0) continue;
-                const MPF<L> v = ld_cg<L>(&slot.row[kc]);
-                if (mpf_better<L>(v, iv, best, bi)) { best = v; bi = iv; bw = q; }
+            constexpr int PER = (COOP_MAXG + 31) / 32;
+            const unsigned want = (unsigned)((c + 1) & 0xfffff);
+            unsigned long long key[PER];
+            bool ok = true;
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int q = tid + 32 * u;
+                key[u] = 0;
+                if (q < G) key[u] = ld_volatile(&sc->part[kc & 1][q].stamp);
             }
-            warp_best<L>(best, bi, bw);
-            if (tid == 0) {
-                s_piv = bi < 0 ? c : bi;
-                s_widx = bw;
-                if (bw >= 0) rec = ld_cg<L>(&sc->part[kc & 1][bw].rec);
+#pragma unroll
+            for (int u = 0; u < PER; ++u) {
+                const int q = tid + 32 * u;
+                if (q < G && ok && (unsigned)(key[u] >> STAMP_SHIFT) != want) {
+                    key[u] = wait_stamp(&sc->part[kc & 1][q].stamp, want, &sc->error);
+                    ok = key[u] != 0;
+                }
+                key[u] &= KEY_MASK;
             }
+            const bool fail = __any_sync(0xffffffffu, !ok);
+            if (!fail) {
+                __threadfence();  // the slots' contents are visible after their stamps
+                unsigned long long K = 0;
+                int W = -1, dummy = 0;
+#pragma unroll
+                for (int u = 0; u < PER; ++u) {
+                    const int q = tid + 32 * u;
+                    if (q < G && key[u] > 0 && (W < 0 || key[u] > K)) { K = key[u]; W = q; }
+                }
+                int Wl = W;
+                warp_best_key(K, Wl, dummy);  // lowest slot among equal keys
+                W = Wl;
+                int same = 0;
+#pragma unroll
+                for (int u = 0; u < PER; ++u) same += (tid + 32 * u < G && key[u] == K) ? 1 : 0;
+                same = __reduce_add_sync(0xffffffffu, same);
+                if (same > 1) {
+                    // equal keys: compare the candidates exactly (lowest row on ties)
+                    MPF<L> v = mpf_make_zero<L>();
+                    int vi = -1, vw = -1;
+#pragma unroll
+                    for (int u = 0; u < PER; ++u) {
+                        const int q = tid + 32 * u;
+                        if (q >= G || key[u] != K) continue;
+                        const CoopSlot<L>& slot = sc->part[kc & 1][q];
+                        const int iv = __ldcg(&slot.idx);
+                        const MPF<L> x = ld_cg<L>(&slot.row[kc]);
+                        if (mpf_better<L>(x, iv, v, vi)) { v = x; vi = iv; vw = q; }
+                    }
+                    warp_best<L>(v, vi, vw);
+                    W = vw;
+                }
+                if (tid == 0) s_widx = W < 0 ? 0 : W;  // W >= 0: the owner of row c has a candidate
+            }
+            if (tid == 0) s_fail = fail ? 1 : 0;
         }
         __syncthreads();
-        const int piv = s_piv;
-        // new row c = the pivot row
-        for (int k = tid; k < b; k += COOP_THREADS)
-            prow[k] = s_widx >= 0 ? ld_cg<L>(&sc->part[kc & 1][s_widx].row[k]) : mpf_make_zero<L>();
+        if (s_fail) return;
+        const int widx = s_widx;
+        // the pivot row, its reciprocal and index, and old row c (for the
+        // owner of the pivot row), all from L2 at once
+        if (tid < b)
+            prow[tid] = ld_cg<L>(&sc->part[kc & 1][widx].row[tid]);
+        else if (tid >= 64 && tid < 64 + b)
+            otmp[tid - 64] = ld_cg<L>(&sc->orow[kc & 1][tid - 64]);
+        else if (tid == 128)
+            rec = ld_cg<L>(&sc->part[kc & 1][widx].rec);
+        else if (tid == 160)
+            s_piv = __ldcg(&sc->part[kc & 1][widx].idx);
         __syncthreads();
+        const int piv = s_piv;
+        if (tid == 0) s_pivs[kc] = piv;
         const bool zero = mpf_zero<L>(prow[kc]);
         if (g == 0 && tid == 0) {
             ipiv[c] = piv + 1;
@@ -508,20 +618,9 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
         }
         if (!zero && piv != c) {
             if (owner(c) == g)
-                for (int k = tid; k < b; k += COOP_THREADS) a[(c - r0) * b + k] = prow[k];
+                for (int k = tid; k < b; k += T) a[(c - r0) * bs + k] = prow[k];
             if (owner(piv) == g)
-                for (int k = tid; k < b; k += COOP_THREADS) a[(piv - r0) * b + k] = ld_cg<L>(&sc->orow[kc & 1][k]);
-            // interchange the rest of the outer panel (global, expansion format)
-            if (g == 0) {
-                const int span = (c0 - p0) + (p1 - c0 - b);
-                for (int t = tid; t < span; t += COOP_THREADS) {
-                    const int j = t < c0 - p0 ? p0 + t : c0 + b + (t - (c0 - p0));
-                    double* x = elem(A, lda, N, c, j);
-                    double* y = elem(A, lda, N, piv, j);
-#pragma unroll
-                    for (int q = 0; q < N; ++q) { const double tt = x[q]; x[q] = y[q]; y[q] = tt; }
-                }
-            }
+                for (int k = tid; k < b; k += T) a[(piv - r0) * bs + k] = otmp[k];
         }
         __syncthreads();
         const int lo = max(r0, c + 1) - r0;
@@ -529,10 +628,10 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
         const int cols = b - kc - 1;
         if (!zero) {
             // multipliers, then the next column first (its candidate is needed next)
-            for (int r = lo + tid; r < nr; r += COOP_THREADS) {
-                const MPF<L> l = mpf_mul<L>(a[r * b + kc], rec);
-                a[r * b + kc] = l;
-                if (cols > 0) a[r * b + kc + 1] = mpf_fms<L>(a[r * b + kc + 1], l, prow[kc + 1]);
+            for (int r = lo + tid; r < nr; r += T) {
+                const MPF<L> l = mpf_mul<L>(a[r * bs + kc], rec);
+                a[r * bs + kc] = l;
+                if (cols > 0) a[r * bs + kc + 1] = mpf_fms<L>(a[r * bs + kc + 1], l, prow[kc + 1]);
             }
         }
         __syncthreads();
@@ -541,21 +640,34 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
         // while the other warps update the remaining columns
         if (tid < 32) {
             candidate(kc + 1, c + 1);
-            if (tid == 0) crec = (ci[0] >= 0 && !mpf_zero<L>(cv[0])) ? mpf_recip<L>(cv[0]) : mpf_make_zero<L>();
         } else if (!zero && cols > 1) {
             const int rest = cols - 1;
             const int total = rows * rest;
-            for (int p = tid - 32; p < total; p += COOP_THREADS - 32) {
+            for (int p = tid - 32; p < total; p += T - 32) {
                 const int r = lo + p / rest, k = kc + 2 + (p - (p / rest) * rest);
-                a[r * b + k] = mpf_fms<L>(a[r * b + k], a[r * b + kc], prow[k]);
+                a[r * bs + k] = mpf_fms<L>(a[r * bs + k], a[r * bs + kc], prow[k]);
             }
         }
         __syncthreads();
         publish(kc + 1);
     }
-    for (int p = tid; p < nr * b; p += COOP_THREADS) {
+    for (int p = tid; p < nr * b; p += T) {
         const int r = p / b, k = p - r * b;
-        mpf_to_exp<L, N>(a[r * b + k], elem(A, lda, N, r0 + r, c0 + k));
+        mpf_to_exp<L, N>(a[r * bs + k], elem(A, lda, N, r0 + r, c0 + k));
+    }
+    // the interchanges of this base block on the rest of the outer panel
+    // (columns [p0, c0) and [c0 + b, p1)), one column per thread
+    const int left = c0 - p0, span = left + (p1 - c0 - b);
+    for (int t = g * T + tid; t < span; t += G * T) {
+        const int j = t < left ? p0 + t : c0 + b + (t - left);
+        for (int kc = 0; kc < b; ++kc) {
+            const int pv = s_pivs[kc], c = c0 + kc;
+            if (pv == c) continue;
+            double* x = elem(A, lda, N, c, j);
+            double* y = elem(A, lda, N, pv, j);
+#pragma unroll
+            for (int q = 0; q < N; ++q) { const double tt = x[q]; x[q] = y[q]; y[q] = tt; }
+        }
     }
 }
 
@@ -792,7 +904,7 @@ bool base_block_coop(double* A, long long lda, int n, int c0, int b, int p0, int
         if (G > COOP_MAXG) G = COOP_MAXG;
         if (G > g_rows) G = g_rows < 1 ? 1 : g_rows;
         const int rows = (n - c0 + G - 1) / G;
-        const size_t smem = sizeof(MPF<L>) * (size_t)rows * b;
+        const size_t smem = sizeof(MPF<L>) * (size_t)rows * (b + 1);
         if (smem > 200 * 1024 / per_sm) continue;
         cudaFuncSetAttribute(base_block_coop_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)(smem < 1024 ? 1024 : smem));
@@ -977,7 +1089,7 @@ namespace {
 // or of a tensor-core GEMM (the handle's error word) gave up
 __global__ void finish_kernel(int* info_out, const LuScratch* sc, const int* coop, const int* gerr) {
     int v = sc->info;
-    if (coop[2]) v = -coop[2];
+    if (coop[0]) v = -coop[0];
     else if (*gerr) v = -*gerr;
     *info_out = v;
 }
@@ -1039,10 +1151,9 @@ int lu_scratch(ozlu_handle* h, LuScratch** out) {
     return OZLU_OK;
 }
 
-// barrier counters and the error word start at zero for every factorisation
+// the error word and the slot stamps start at zero for every factorisation
 int coop_reset(ozlu_handle* h, cudaStream_t s) {
-    return cudaMemsetAsync(h->coop_scratch, 0, 4 * sizeof(int), s) == cudaSuccess ? OZLU_OK
-                                                                                   : OZLU_ERR_CUDA;
+    return cudaMemsetAsync(h->coop_scratch, 0, h->coop_bytes, s) == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
 }
 
 // waits for the stream; OZLU_ERR_TIMEOUT if a bounded device wait gave up

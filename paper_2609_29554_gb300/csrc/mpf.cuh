@@ -57,20 +57,19 @@ __device__ __forceinline__ MPF<L> mpf_round(uint32_t (&X)[W], int ex, int neg, b
         for (int i = W - 1; i > 0; --i) X[i] = __funnelshift_l(X[i - 1], X[i], sh);
         X[0] <<= sh;
     } else if (sh >= 32) {
+        // whole words by a logarithmic shifter (selects, no dynamic indexing), then bits
         const int q = sh >> 5, rr = sh & 31;
-        uint32_t T[W];
 #pragma unroll
-        for (int i = W - 1; i >= 0; --i) {
-            uint32_t hi = 0, lo = 0;
+        for (int s = 8; s >= 1; s >>= 1) {
+            if (s < W) {
+                const bool on = (q & s) != 0;
 #pragma unroll
-            for (int k = 0; k < W; ++k) {
-                if (k == i - q) hi = X[k];
-                if (k == i - q - 1) lo = X[k];
+                for (int i = W - 1; i >= 0; --i) X[i] = on ? (i >= s ? X[i - s] : 0u) : X[i];
             }
-            T[i] = rr ? (hi << rr) | (lo >> (32 - rr)) : hi;
         }
 #pragma unroll
-        for (int i = 0; i < W; ++i) X[i] = T[i];
+        for (int i = W - 1; i > 0; --i) X[i] = __funnelshift_l(X[i - 1], X[i], rr);
+        X[0] <<= rr;
     }
     ex -= sh;
     // top L words; round bit = top bit of word W-L-1; sticky = the rest
@@ -201,19 +200,26 @@ __device__ __forceinline__ int mpf_abs_cmp(const MPF<L>& a, const MPF<L>& b) {
 template <int L>
 __device__ __forceinline__ MPF<L> mpf_mul(const MPF<L>& a, const MPF<L>& b) {
     if (mpf_zero<L>(a) || mpf_zero<L>(b)) return mpf_make_zero<L>();
-    uint32_t P[2 * L];
+    // column sums of the 32-bit halves of the limb products (independent,
+    // each below 2^(33 + log2 L)), then one carry pass
+    uint64_t S[2 * L];
 #pragma unroll
-    for (int i = 0; i < 2 * L; ++i) P[i] = 0;
+    for (int k = 0; k < 2 * L; ++k) S[k] = 0;
 #pragma unroll
-    for (int i = 0; i < L; ++i) {
-        uint64_t c = 0;
+    for (int i = 0; i < L; ++i)
 #pragma unroll
         for (int j = 0; j < L; ++j) {
-            const uint64_t t = (uint64_t)a.m[i] * b.m[j] + P[i + j] + c;
-            P[i + j] = (uint32_t)t;
-            c = t >> 32;
+            const uint64_t t = (uint64_t)a.m[i] * b.m[j];
+            S[i + j] += (uint32_t)t;
+            S[i + j + 1] += t >> 32;
         }
-        P[i + L] = (uint32_t)c;
+    uint32_t P[2 * L];
+    uint64_t c = 0;
+#pragma unroll
+    for (int k = 0; k < 2 * L; ++k) {
+        const uint64_t v = S[k] + c;
+        P[k] = (uint32_t)v;
+        c = v >> 32;
     }
     // value = P * 2^(a.e + b.e - 64 L) = P * 2^((a.e + b.e) - 32 * 2L)
     return mpf_round<L, 2 * L>(P, a.e + b.e, a.neg ^ b.neg, false);
@@ -231,38 +237,39 @@ __device__ __forceinline__ MPF<L> mpf_add(const MPF<L>& a, const MPF<L>& b) {
     uint32_t X[W], Y[W];
     X[0] = 0;
     X[1] = 0;
+    Y[0] = 0;
+    Y[1] = 0;
 #pragma unroll
-    for (int i = 0; i < L; ++i) X[i + 2] = x.m[i];
-    // y shifted right by d = x.e - y.e bits into the same window
+    for (int i = 0; i < L; ++i) {
+        X[i + 2] = x.m[i];
+        Y[i + 2] = y.m[i];
+    }
+    // y shifted right by d = x.e - y.e bits (whole words by a logarithmic
+    // shifter, then bits); sticky collects the bits shifted out
     const int d = x.e - y.e;
     bool sticky = false;
+    if (d >= 32 * W) {
 #pragma unroll
-    for (int i = 0; i < W; ++i) Y[i] = 0;
-    if (d < 32 * W) {
+        for (int i = 0; i < W; ++i) Y[i] = 0;
+        sticky = true;
+    } else {
         const int q = d >> 5, r = d & 31;
 #pragma unroll
-        for (int i = 0; i < W; ++i) {
-            // Y[i] = bits of (y.m << 64) >> d at word i
-            uint32_t lo = 0, hi = 0;
+        for (int s = 8; s >= 1; s >>= 1) {
+            if (s < W) {
+                const bool on = (q & s) != 0;
+                uint32_t lost = 0;
 #pragma unroll
-            for (int k = 0; k < L; ++k) {
-                if (k + 2 == i + q) lo = y.m[k];
-                if (k + 2 == i + q + 1) hi = y.m[k];
-            }
-            Y[i] = r ? (lo >> r) | (hi << (32 - r)) : lo;
-        }
-        // sticky: bits of y shifted out below the window
+                for (int i = 0; i < s; ++i) lost |= Y[i];
+                sticky |= on && lost != 0;
 #pragma unroll
-        for (int k = 0; k < L; ++k) {
-            const int lowbit = 32 * (k + 2) - d;  // position of y.m[k] bit 0 in the window
-            if (lowbit < 0) {
-                const int keep_from = -lowbit;  // bits of y.m[k] below this are lost
-                if (keep_from >= 32) sticky |= y.m[k] != 0;
-                else sticky |= (y.m[k] & ((1u << keep_from) - 1u)) != 0;
+                for (int i = 0; i < W; ++i) Y[i] = on ? (i + s < W ? Y[i + s] : 0u) : Y[i];
             }
         }
-    } else {
-        sticky = true;
+        sticky |= r != 0 && (Y[0] & ((1u << r) - 1u)) != 0;
+#pragma unroll
+        for (int i = 0; i < W - 1; ++i) Y[i] = __funnelshift_r(Y[i], Y[i + 1], r);
+        Y[W - 1] >>= r;
     }
     if (x.neg == y.neg) {
         uint64_t c = 0;
@@ -311,20 +318,33 @@ __device__ __forceinline__ MPF<L> mpf_from_double(double v) {
     return mpf_from_exp<L, 1>(&v);
 }
 
-// 1 / b by Newton's iteration r <- r (2 - b r) from a binary64 start
+// 1 / b by Newton's iteration r <- r (2 - f r) (quadratic convergence) on the
+// mantissa f = |b| 2^-e in [1/2, 1), from a double-double start: with
+// fh + fl the top 106 bits of f, r0 = 1 / fh (correctly rounded),
+// e = 1 - (fh + fl) r0 from two fused multiply-adds (the first is exact), and
+// r0 + r0 e is 1 / f to about 104 bits.  Steps double that until it covers
+// the 32 L bits of the format; the exponent is applied last, so no binary64
+// quantity over- or underflows whatever the exponent of b.
 template <int L>
 __device__ __forceinline__ MPF<L> mpf_recip(const MPF<L>& b) {
-    // binary64 approximation of b
-    double bd[1];
-    {
-        const uint64_t top = ((uint64_t)b.m[L - 1] << 32) | b.m[L - 2];
-        double v = scalbn((double)(top >> 11), b.e - 53);
-        bd[0] = b.neg ? -v : v;
-    }
-    MPF<L> r = mpf_from_double<L>(1.0 / bd[0]);
+    static_assert(L >= 4, "double-double start needs 4 limbs");
+    const uint64_t top = ((uint64_t)b.m[L - 1] << 32) | b.m[L - 2];
+    const uint64_t nxt = ((uint64_t)b.m[L - 3] << 32) | b.m[L - 4];
+    // f = m 2^(-32 L) ~ top 2^-64: fh = top[63:11] 2^-53, fl = the next 53 bits 2^-106
+    const double fh = scalbn((double)(top >> 11), -53);
+    const double fl = scalbn((double)(((top & 0x7ffull) << 42) | (nxt >> 22)), -106);
+    const double r0 = 1.0 / fh;
+    double e = fma(-fh, r0, 1.0);
+    e = fma(-fl, r0, e);
+    const double seed[2] = {r0, r0 * e};
+    MPF<L> r = mpf_from_exp<L, 2>(seed);
+    MPF<L> f = b;
+    f.neg = 0;
+    f.e = 0;
     const MPF<L> two = mpf_from_double<L>(2.0);
-    // 53 -> 106 -> 212 -> 424 bits
-    for (int it = 0; it < 4 && (53 << it) < 32 * L + 53; ++it) r = mpf_mul<L>(r, mpf_sub<L>(two, mpf_mul<L>(b, r)));
+    for (int prec = 104; prec < 32 * L + 8; prec *= 2) r = mpf_mul<L>(r, mpf_sub<L>(two, mpf_mul<L>(f, r)));
+    r.e -= b.e;
+    r.neg = b.neg;
     return r;
 }
 
