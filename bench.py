@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--nmin", type=int, default=64)
     ap.add_argument("--nmax", type=int, default=1024)
     ap.add_argument("--backend", default="auto")
+    ap.add_argument("--panel-width", type=int, default=0,
+                    help="widest cooperative panel block (32/64/128; 0 = library choice)")
     ap.add_argument("--compare", action="store_true",
                     help="also time the single-instance INT8 Ozaki-II LU and the native "
                          "(blocked-naive) expansion LU on the same matrix")
@@ -431,7 +433,7 @@ def main_batched(a, rank, world, local, ozlu, torch):
     gen_s = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     h = ozlu.ozlu_create(stream)
-    opts = ozlu.make_opts(a.backend, graph=1)
+    opts = ozlu.make_opts(a.backend, graph=1, panel_width=a.panel_width)
 
     def step():
         bt.restore()
@@ -465,7 +467,7 @@ def main_batched(a, rank, world, local, ozlu, torch):
     # were warmed by the graph's first call)
     bt.restore()
     ozlu.ozlu_set_timing(h, 1)
-    bt.solve(ozlu, h, nc, nb, ozlu.make_opts(a.backend))
+    bt.solve(ozlu, h, nc, nb, ozlu.make_opts(a.backend, panel_width=a.panel_width))
     torch.cuda.synchronize()
     stp = ozlu.ozlu_get_stats(h)
     ozlu.ozlu_set_timing(h, 0)
@@ -556,7 +558,7 @@ def main():
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     h = ozlu.ozlu_create(stream)
-    opts = ozlu.make_opts(a.backend, graph=1)
+    opts = ozlu.make_opts(a.backend, graph=1, panel_width=a.panel_width)
     flops = 2.0 * n ** 3 / 3.0
 
     def step():
@@ -591,7 +593,8 @@ def main():
     for timed in (0, 1):
         A.copy_(A0)
         ozlu.ozlu_set_timing(h, timed)
-        ozlu.ozlu_getrf(h, nc, 0, n, A, n, ipiv, nb, info, ozlu.make_opts(a.backend))
+        ozlu.ozlu_getrf(h, nc, 0, n, A, n, ipiv, nb, info,
+                        ozlu.make_opts(a.backend, panel_width=a.panel_width))
         torch.cuda.synchronize()
     stp = ozlu.ozlu_get_stats(h)
     ozlu.ozlu_set_timing(h, 0)

@@ -76,7 +76,9 @@ typedef struct {
                          second call with the same sizes and pointers and replay it
                          from then on (no host synchronisation inside the call; a
                          bounded-wait timeout shows in info, see the batched LU) */
-    int reserved[10];
+    int panel_width;  /* ozlu_getrf: widest base block of the cooperative panel kernel
+                         (32, 64 or 128; 0 = chosen from the rows per thread block) */
+    int reserved[9];
 } ozlu_opts;
 
 /* Plan of one Ozaki-II GEMM (Sec. 3.2 "Determining w and N"). */

@@ -40,6 +40,12 @@ int ensure_subs(ozlu_handle* h) {
     return OZLU_OK;
 }
 
+// every option field is part of a graph's key (a graph replays one configuration)
+void append_opts(std::vector<long long>& key, const ozlu_opts& o) {
+    const int* w = reinterpret_cast<const int*>(&o);
+    for (size_t i = 0; i < sizeof(ozlu_opts) / sizeof(int); ++i) key.push_back(w[i]);
+}
+
 // greedy assignment of instances (largest first) to the least-loaded stream
 std::vector<std::vector<int>> assign(int count, const int* n) {
     std::vector<int> order(count);
@@ -211,8 +217,8 @@ extern "C" int ozlu_getrf_batched(ozlu_handle* h, int nc, int p, int count, cons
     ozlu_opts o;
     memset(&o, 0, sizeof o);
     if (opts) o = *opts;
-    std::vector<long long> key{1, nc, p, count, nb, o.backend, o.nslice, o.extra_groups, o.g_ex, o.native,
-                               (long long)info};
+    std::vector<long long> key{1, nc, p, count, nb, (long long)info};
+    append_opts(key, o);
     for (int i = 0; i < count; ++i) {
         key.push_back(n[i]);
         key.push_back((long long)A[i]);
@@ -251,7 +257,8 @@ extern "C" int ozlu_getrs_batched(ozlu_handle* h, int nc, int p, int count, cons
     ozlu_opts o;
     memset(&o, 0, sizeof o);
     if (opts) o = *opts;
-    std::vector<long long> key{2, nc, p, count, nrhs, o.backend, o.nslice, o.extra_groups, o.g_ex};
+    std::vector<long long> key{2, nc, p, count, nrhs};
+    append_opts(key, o);
     for (int i = 0; i < count; ++i) {
         key.push_back(n[i]);
         key.push_back((long long)LU[i]);

@@ -25,7 +25,8 @@
 namespace ozlu {
 namespace {
 
-constexpr int BASE = 32;        // base-block width of the recursion
+constexpr int BASE = 32;        // triangular-solve leaves and the fallback panel path
+constexpr int PBASE = 128;      // widest base block of the cooperative panel kernel
 constexpr int PIV_THREADS = 256;
 constexpr int PIV_BLOCKS = 152;
 constexpr int MAXPART = 1024;   // block partials of a column step
@@ -335,6 +336,7 @@ __global__ void __launch_bounds__(128) column_step_kernel(double* A, long long l
 // records OZLU_ERR_TIMEOUT in the scratch and every block returns.
 constexpr int COOP_MAXG = 304;           // blocks (up to 2 per SM)
 constexpr int COOP_THREADS = 512;
+static_assert(2 * PBASE + 2 <= COOP_THREADS, "one pivot-row element per thread");
 constexpr unsigned long long COOP_WAIT_NS = 2000000000ull;
 
 // stamp word of a slot: bits 63..44 the column (c0 + kc + 1, modulo 2^20),
@@ -349,7 +351,7 @@ struct CoopSlot {
     int idx;                 // the candidate's global row index, -1 if none
     int pad;
     MPF<L> rec;              // 1 / the candidate (0 for a zero candidate)
-    MPF<L> row[BASE];        // the candidate row (all b columns)
+    MPF<L> row[PBASE];       // the candidate row (all b columns)
 };
 
 template <int L>
@@ -357,8 +359,17 @@ struct CoopScratch {
     int error;
     int pad[3];
     CoopSlot<L> part[2][COOP_MAXG];  // double-buffered by column parity
-    MPF<L> orow[2][BASE];            // old row c, for the owner of the pivot row
+    MPF<L> orow[2][PBASE];           // old row c, for the owner of the pivot row
 };
+
+// the error word and every slot stamp start at zero for each factorisation
+// (one thread per slot; the scratch was laid out for L limbs)
+template <int L>
+__global__ void coop_reset_kernel(CoopScratch<L>* sc) {
+    const int t = threadIdx.x;
+    if (t == 0) sc->error = 0;
+    if (t < 2 * COOP_MAXG) sc->part[t / COOP_MAXG][t % COOP_MAXG].stamp = 0ull;
+}
 
 __device__ __forceinline__ unsigned long long global_ns() {
     unsigned long long t;
@@ -460,13 +471,13 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
     // rows padded to b + 1 entries: threads on consecutive rows of one column
     // then fall on different shared-memory banks
     const int bs = b + 1;
-    __shared__ MPF<L> prow[BASE];  // the pivot row
-    __shared__ MPF<L> otmp[BASE];  // old row c (for the owner of the pivot row)
+    __shared__ MPF<L> prow[PBASE];  // the pivot row
+    __shared__ MPF<L> otmp[PBASE];  // old row c (for the owner of the pivot row)
     __shared__ MPF<L> rec;         // 1 / pivot
     __shared__ MPF<L> crec;        // 1 / this block's next candidate
     __shared__ MPF<L> cv;          // this block's next candidate
     __shared__ int ci, s_piv, s_widx, s_fail;
-    __shared__ int s_pivs[BASE];
+    __shared__ int s_pivs[PBASE];
     const int g = blockIdx.x, G = gridDim.x, tid = threadIdx.x;
     const int r0 = c0 + g * rows_per_block;
     const int r1 = min(n, r0 + rows_per_block);
@@ -600,13 +611,14 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
         const int widx = s_widx;
         // the pivot row, its reciprocal and index, and old row c (for the
         // owner of the pivot row), all from L2 at once
+        // (b <= PBASE < T / 2 - 1: one element per thread)
         if (tid < b)
             prow[tid] = ld_cg<L>(&sc->part[kc & 1][widx].row[tid]);
-        else if (tid >= 64 && tid < 64 + b)
-            otmp[tid - 64] = ld_cg<L>(&sc->orow[kc & 1][tid - 64]);
-        else if (tid == 128)
+        else if (tid < 2 * b)
+            otmp[tid - b] = ld_cg<L>(&sc->orow[kc & 1][tid - b]);
+        else if (tid == 2 * b)
             rec = ld_cg<L>(&sc->part[kc & 1][widx].rec);
-        else if (tid == 160)
+        else if (tid == 2 * b + 1)
             s_piv = __ldcg(&sc->part[kc & 1][widx].idx);
         __syncthreads();
         const int piv = s_piv;
@@ -835,8 +847,11 @@ __global__ void __launch_bounds__(256) tri_convert_kernel(const double* T, long 
 
 // X <- L^-1 X for a unit lower (lower = 1) or U^-1 X for an upper (lower = 0,
 // non-unit) b x b triangle, b <= BASE; X is b x ncols.  L-limb integer
-// floating point; a block of 32 x cpb threads owns cpb columns, thread
-// (row, column) updates its element after each pivot row is final.
+// floating point.  One warp per column, lane i holding x_i in registers: step
+// k broadcasts the final x_k by warp shuffles and every lane below (lower) or
+// above (upper) row k subtracts l_ik x_k, so the b steps need no block-wide
+// barrier and the warps of a block progress independently.  The triangle is
+// read from shared memory column by column ([k][i], conflict-free).
 template <int N>
 __global__ void __launch_bounds__(256) trsm_base_kernel(const LuScratch* sc, double* X, long long ldx, int b,
                                                         int ncols, int lower) {
@@ -844,29 +859,27 @@ __global__ void __launch_bounds__(256) trsm_base_kernel(const LuScratch* sc, dou
     extern __shared__ __align__(16) unsigned char smraw[];
     MPF<L>* sl = reinterpret_cast<MPF<L>*>(smraw);   // [k][i]
     MPF<L>* rd = sl + BASE * BASE;                   // reciprocal diagonal (upper)
-    MPF<L>* sx = rd + BASE;                          // [cc][i]
-    const int cpb = blockDim.x >> 5;
-    const int row = threadIdx.x & 31, cc = threadIdx.x >> 5;
-    const int col = blockIdx.x * cpb + cc;
+    const int row = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int col = blockIdx.x * (blockDim.x >> 5) + w;
     const MPF<L>* tl = reinterpret_cast<const MPF<L>*>(sc->tri);
     for (int idx = threadIdx.x; idx < BASE * BASE; idx += blockDim.x) sl[idx] = tl[idx];
     if (!lower)
         for (int k = threadIdx.x; k < b; k += blockDim.x) rd[k] = tl[BASE * BASE + k];
-    if (row < b)
-        sx[cc * BASE + row] = col < ncols ? mpf_from_exp<L, N>(X + ((long long)row + (long long)col * ldx) * N)
-                                          : mpf_make_zero<L>();
     __syncthreads();
+    if (col >= ncols) return;  // whole warps: col is uniform in a warp
+    double* xp = X + ((long long)row + (long long)col * ldx) * N;
+    MPF<L> x = row < b ? mpf_from_exp<L, N>(xp) : mpf_make_zero<L>();
     for (int s = 0; s < b; ++s) {
         const int k = lower ? s : b - 1 - s;
-        if (!lower) {
-            if (row == k) sx[cc * BASE + k] = mpf_mul<L>(sx[cc * BASE + k], rd[k]);
-            __syncthreads();
-        }
-        if (row < b && ((lower && row > k) || (!lower && row < k)))
-            sx[cc * BASE + row] = mpf_fms<L>(sx[cc * BASE + row], sl[k * BASE + row], sx[cc * BASE + k]);
-        __syncthreads();
+        if (!lower && row == k) x = mpf_mul<L>(x, rd[k]);
+        MPF<L> xk;
+#pragma unroll
+        for (int q = 0; q < L; ++q) xk.m[q] = __shfl_sync(0xffffffffu, x.m[q], k);
+        xk.e = __shfl_sync(0xffffffffu, x.e, k);
+        xk.neg = __shfl_sync(0xffffffffu, x.neg, k);
+        if (row < b && (lower ? row > k : row < k)) x = mpf_fms<L>(x, sl[k * BASE + row], xk);
     }
-    if (row < b && col < ncols) mpf_to_exp<L, N>(sx[cc * BASE + row], X + ((long long)row + (long long)col * ldx) * N);
+    if (row < b) mpf_to_exp<L, N>(x, xp);
 }
 
 template <int N>
@@ -875,16 +888,15 @@ void trsm_base(const double* T, long long ldt, double* X, long long ldx, int b, 
     if (ncols <= 0 || b <= 0) return;
     constexpr int L = Limbs<N>::L;
     tri_convert_kernel<N><<<(b * b + 255) / 256, 256, 0, s>>>(T, ldt, b, lower, sc);
-    int cpb = ncols / 304;
-    cpb = cpb < 1 ? 1 : (cpb > 8 ? 8 : cpb);
-    const size_t smem = sizeof(MPF<L>) * (BASE * BASE + BASE + BASE * cpb);
+    // 8 columns (warps) per block, fewer when that leaves SMs idle
+    const int wpb = ncols >= 8 * 152 ? 8 : (ncols >= 4 * 152 ? 4 : 2);
+    const size_t smem = sizeof(MPF<L>) * (BASE * BASE + BASE);
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(trsm_base_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(MPF<L>) * (BASE * BASE + BASE + BASE * 8)));
+        cudaFuncSetAttribute(trsm_base_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    trsm_base_kernel<N><<<(ncols + cpb - 1) / cpb, 32 * cpb, smem, s>>>(sc, X, ldx, b, ncols, lower);
+    trsm_base_kernel<N><<<(ncols + wpb - 1) / wpb, 32 * wpb, smem, s>>>(sc, X, ldx, b, ncols, lower);
 }
 
 // Launch the cooperative base-block kernel; returns false when the slice of
@@ -948,6 +960,14 @@ struct Ctx {
 
 double* at(const Ctx& c, long long i, long long j) { return c.A + (i + j * c.lda) * c.nc; }
 
+// widest base block for the cooperative panel kernel: the caller's choice,
+// else PBASE (measured fastest on GB300 for n from 512 to 4096; a block
+// whose rows do not fit in shared memory is split by the recursion)
+int coop_width(const Ctx& c, int) {
+    if (c.opts && c.opts->panel_width) return c.opts->panel_width < PBASE ? c.opts->panel_width : PBASE;
+    return PBASE;
+}
+
 template <int N>
 void trsm_rec(Ctx& c, long long r, int b, long long j0, int ncols, bool lower) {
     if (c.rc || ncols <= 0) return;
@@ -977,13 +997,17 @@ template <int N>
 void panel_rec(Ctx& c, int r, int b, int p0, int p1) {
     if (c.rc) return;
     cudaStream_t s = c.h->stream;
-    if (b <= BASE) {
+    // up to coop_width columns in one cooperative kernel when its rows fit
+    // in shared memory (else the block is split further)
+    if (b <= coop_width(c, r)) {
         c.h->phase(PH_PANEL);
         if (base_block_coop<N>(c.A, c.lda, c.n, r, b, p0, p1, c.ipiv, &c.sc->info, c.h->coop_scratch, s)) {
             c.h->count(1);
             c.h->stats.panel_launches += 1;
             return;
         }
+    }
+    if (b <= BASE) {
         c.h->count(1 + b);
         c.h->stats.panel_launches += 1 + b;
         {
@@ -1081,7 +1105,7 @@ size_t align256(size_t v) { return (v + 255) / 256 * 256; }
 }  // namespace
 
 int lu_scratch(ozlu_handle* h, LuScratch** out);
-int coop_reset(ozlu_handle* h, cudaStream_t s);
+int coop_reset(ozlu_handle* h, int nc, cudaStream_t s);
 
 namespace {
 // info of one factorisation: the first zero pivot (1-based), or
@@ -1104,7 +1128,7 @@ int getrf_one(ozlu_handle* h, int nc, int p, int n, double* A, long long lda, in
     if (rc) return rc;
     cudaStream_t s = h->stream;
     if (cudaMemsetAsync(sc, 0, sizeof(LuScratch), s)) return OZLU_ERR_CUDA;
-    if ((rc = coop_reset(h, s))) return rc;
+    if ((rc = coop_reset(h, nc, s))) return rc;
     if ((rc = clear_err_word(h))) return rc;
     if (n > 0) {
         switch (nc) {
@@ -1152,8 +1176,14 @@ int lu_scratch(ozlu_handle* h, LuScratch** out) {
 }
 
 // the error word and the slot stamps start at zero for every factorisation
-int coop_reset(ozlu_handle* h, cudaStream_t s) {
-    return cudaMemsetAsync(h->coop_scratch, 0, h->coop_bytes, s) == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
+int coop_reset(ozlu_handle* h, int nc, cudaStream_t s) {
+    switch (nc) {
+        case 2: coop_reset_kernel<4><<<1, 2 * COOP_MAXG, 0, s>>>((CoopScratch<4>*)h->coop_scratch); break;
+        case 3: coop_reset_kernel<6><<<1, 2 * COOP_MAXG, 0, s>>>((CoopScratch<6>*)h->coop_scratch); break;
+        default: coop_reset_kernel<8><<<1, 2 * COOP_MAXG, 0, s>>>((CoopScratch<8>*)h->coop_scratch); break;
+    }
+    h->count(1);
+    return cudaGetLastError() == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
 }
 
 // waits for the stream; OZLU_ERR_TIMEOUT if a bounded device wait gave up

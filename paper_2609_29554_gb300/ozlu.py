@@ -34,7 +34,7 @@ class ozlu_opts(ctypes.Structure):
     _fields_ = [("backend", ctypes.c_int), ("nslice", ctypes.c_int),
                 ("extra_groups", ctypes.c_int), ("g_ex", ctypes.c_int),
                 ("native", ctypes.c_int), ("graph", ctypes.c_int),
-                ("reserved", ctypes.c_int * 10)]
+                ("panel_width", ctypes.c_int), ("reserved", ctypes.c_int * 9)]
 
 
 class ozlu_plan_info(ctypes.Structure):
@@ -102,10 +102,11 @@ def _check(fn, code):
         raise OzluError(fn, code)
 
 
-def make_opts(backend="int8", nslice=0, extra_groups=0, g_ex=0, native=0, graph=0):
+def make_opts(backend="int8", nslice=0, extra_groups=0, g_ex=0, native=0, graph=0, panel_width=0):
     o = ozlu_opts()
     o.backend = BACKENDS[backend] if isinstance(backend, str) else int(backend)
     o.nslice, o.extra_groups, o.g_ex, o.native, o.graph = nslice, extra_groups, g_ex, native, graph
+    o.panel_width = panel_width
     return o
 
 
