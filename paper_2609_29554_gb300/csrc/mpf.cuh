@@ -196,12 +196,12 @@ __device__ __forceinline__ int mpf_abs_cmp(const MPF<L>& a, const MPF<L>& b) {
     return 0;
 }
 
-// a * b, rounded to L words
+// Exact product of two L-word magnitudes (2 L words): column sums of the
+// 32-bit halves of the limb products (independent, each below
+// 2^(33 + log2 L)), then one carry pass.  (Carry-flag chains of 32-bit
+// multiply-adds measured slower on GB300: they serialise on the flag.)
 template <int L>
-__device__ __forceinline__ MPF<L> mpf_mul(const MPF<L>& a, const MPF<L>& b) {
-    if (mpf_zero<L>(a) || mpf_zero<L>(b)) return mpf_make_zero<L>();
-    // column sums of the 32-bit halves of the limb products (independent,
-    // each below 2^(33 + log2 L)), then one carry pass
+__device__ __forceinline__ void mul_words(const uint32_t (&a)[L], const uint32_t (&b)[L], uint32_t (&P)[2 * L]) {
     uint64_t S[2 * L];
 #pragma unroll
     for (int k = 0; k < 2 * L; ++k) S[k] = 0;
@@ -209,11 +209,10 @@ __device__ __forceinline__ MPF<L> mpf_mul(const MPF<L>& a, const MPF<L>& b) {
     for (int i = 0; i < L; ++i)
 #pragma unroll
         for (int j = 0; j < L; ++j) {
-            const uint64_t t = (uint64_t)a.m[i] * b.m[j];
+            const uint64_t t = (uint64_t)a[i] * b[j];
             S[i + j] += (uint32_t)t;
             S[i + j + 1] += t >> 32;
         }
-    uint32_t P[2 * L];
     uint64_t c = 0;
 #pragma unroll
     for (int k = 0; k < 2 * L; ++k) {
@@ -221,6 +220,14 @@ __device__ __forceinline__ MPF<L> mpf_mul(const MPF<L>& a, const MPF<L>& b) {
         P[k] = (uint32_t)v;
         c = v >> 32;
     }
+}
+
+// a * b, rounded to L words
+template <int L>
+__device__ __forceinline__ MPF<L> mpf_mul(const MPF<L>& a, const MPF<L>& b) {
+    if (mpf_zero<L>(a) || mpf_zero<L>(b)) return mpf_make_zero<L>();
+    uint32_t P[2 * L];
+    mul_words<L>(a.m, b.m, P);
     // value = P * 2^(a.e + b.e - 64 L) = P * 2^((a.e + b.e) - 32 * 2L)
     return mpf_round<L, 2 * L>(P, a.e + b.e, a.neg ^ b.neg, false);
 }
@@ -307,10 +314,147 @@ __device__ __forceinline__ MPF<L> mpf_sub(const MPF<L>& a, const MPF<L>& b) {
     return mpf_add<L>(a, mpf_neg<L>(b));
 }
 
-// c - a b (two roundings)
+// Y >>= d bits (d >= 0) by a logarithmic word shifter and a funnel shift;
+// sticky collects the bits shifted out
+template <int W>
+__device__ __forceinline__ void shr_sticky(uint32_t (&Y)[W], int d, bool& sticky) {
+    if (d >= 32 * W) {
+        bool any = false;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            any |= Y[i] != 0;
+            Y[i] = 0;
+        }
+        sticky |= any;
+        return;
+    }
+    const int q = d >> 5, r = d & 31;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        if (s < W) {
+            const bool on = (q & s) != 0;
+            uint32_t lost = 0;
+#pragma unroll
+            for (int i = 0; i < s; ++i) lost |= Y[i];
+            sticky |= on && lost != 0;
+#pragma unroll
+            for (int i = 0; i < W; ++i) Y[i] = on ? (i + s < W ? Y[i + s] : 0u) : Y[i];
+        }
+    }
+    sticky |= r != 0 && (Y[0] & ((1u << r) - 1u)) != 0;
+#pragma unroll
+    for (int i = 0; i < W - 1; ++i) Y[i] = __funnelshift_r(Y[i], Y[i + 1], r);
+    Y[W - 1] >>= r;
+}
+
+// (-1)^xn X 2^(ex - 32 W) + (-1)^yn Y 2^(ey - 32 W), both W-word magnitudes
+// normalised (top bit set) or zero (xz, yz), rounded to L words; ysticky:
+// Y stands for a value with more nonzero bits below its last word
+template <int L, int W>
+__device__ __forceinline__ MPF<L> add_windows(uint32_t (&X)[W], int ex, int xn, bool xz, uint32_t (&Y)[W], int ey,
+                                              int yn, bool yz, bool ysticky) {
+    if (yz) return mpf_round<L, W>(X, ex, xn, false);
+    if (xz) return mpf_round<L, W>(Y, ey, yn, ysticky);
+    bool swap = ey > ex;  // |Y| > |X|
+    if (ey == ex) {
+        int cmp = 0;
+#pragma unroll
+        for (int i = W - 1; i >= 0; --i)
+            if (cmp == 0 && X[i] != Y[i]) cmp = X[i] > Y[i] ? 1 : -1;
+        swap = cmp < 0;
+    }
+    uint32_t A[W], B[W];
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        A[i] = swap ? Y[i] : X[i];
+        B[i] = swap ? X[i] : Y[i];
+    }
+    const int ea = swap ? ey : ex, eb = swap ? ex : ey;
+    const int an = swap ? yn : xn, bn = swap ? xn : yn;
+    bool sticky = swap ? false : ysticky;
+    shr_sticky<W>(B, ea - eb, sticky);
+    if (an == bn) {
+        uint64_t c = 0;
+#pragma unroll
+        for (int i = 0; i < W; ++i) {
+            const uint64_t s = (uint64_t)A[i] + B[i] + c;
+            A[i] = (uint32_t)s;
+            c = s >> 32;
+        }
+        if (c) {
+            sticky |= (A[0] & 1u) != 0;
+#pragma unroll
+            for (int i = 0; i < W - 1; ++i) A[i] = (A[i] >> 1) | (A[i + 1] << 31);
+            A[W - 1] = (A[W - 1] >> 1) | 0x80000000u;
+            return mpf_round<L, W>(A, ea + 1, an, sticky);
+        }
+        return mpf_round<L, W>(A, ea, an, sticky);
+    }
+    // the exact difference is A - B - delta with 0 <= delta < 1 unit of the
+    // window: A - B - 1 plus a set sticky stands for it whenever delta > 0
+    uint64_t brw = sticky ? 1u : 0u;
+#pragma unroll
+    for (int i = 0; i < W; ++i) {
+        const uint64_t s = (uint64_t)A[i] - B[i] - brw;
+        A[i] = (uint32_t)s;
+        brw = (s >> 63) & 1u;
+    }
+    return mpf_round<L, W>(A, ea, an, sticky);
+}
+
+// c - a b with one rounding: the product's top L + 2 words (words L - 2 ..
+// 2L - 1 of the 2L-word product, from the limb products that reach them; the
+// carry lost from the words below is under 2^5 units of the lowest window
+// word) are added to c in an (L + 2)-word window, the lower words counting as
+// a set sticky.  The result is the correctly rounded c - a b unless the exact
+// value lies within about 2^-58 of a unit of its last word from a rounding
+// boundary.
 template <int L>
 __device__ __forceinline__ MPF<L> mpf_fms(const MPF<L>& c, const MPF<L>& a, const MPF<L>& b) {
-    return mpf_sub<L>(c, mpf_mul<L>(a, b));
+    static_assert(L >= 4, "two guard words below the product window");
+    constexpr int W = L + 2;
+    if (mpf_zero<L>(a) || mpf_zero<L>(b)) return c;
+    // window word k = product word k + L - 2: lo(a_i b_j) for i + j >= L - 2,
+    // hi(a_i b_j) for i + j >= L - 3
+    uint64_t S[W + 1];
+#pragma unroll
+    for (int k = 0; k <= W; ++k) S[k] = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i)
+#pragma unroll
+        for (int j = 0; j < L; ++j) {
+            const int k = i + j - (L - 2);
+            if (k >= 0) {
+                const uint64_t t = (uint64_t)a.m[i] * b.m[j];
+                S[k] += (uint32_t)t;
+                S[k + 1] += t >> 32;
+            } else if (k == -1) {
+                S[0] += __umulhi(a.m[i], b.m[j]);
+            }
+        }
+    uint32_t P[W];
+    uint64_t cy = 0;
+#pragma unroll
+    for (int k = 0; k < W; ++k) {
+        const uint64_t v = S[k] + cy;
+        P[k] = (uint32_t)v;
+        cy = v >> 32;
+    }
+    // a b ~ P 2^(ep - 32 W); normalise (the top bit may be clear)
+    int ep = a.e + b.e;
+    if (!(P[W - 1] >> 31)) {
+#pragma unroll
+        for (int i = W - 1; i > 0; --i) P[i] = __funnelshift_l(P[i - 1], P[i], 1);
+        P[0] <<= 1;
+        ep -= 1;
+    }
+    const bool sticky = true;
+    uint32_t C[W];
+    C[0] = 0;
+    C[1] = 0;
+#pragma unroll
+    for (int i = 0; i < L; ++i) C[i + 2] = c.m[i];
+    return add_windows<L, W>(C, c.e, c.neg, mpf_zero<L>(c), P, ep, a.neg ^ b.neg ^ 1, false, sticky);
 }
 
 template <int L>
