@@ -13,11 +13,14 @@
 // Both rely on the fp32 tensor-core accumulation being exact for integer
 // sums below 2^24; the parity tests check it bit for bit.
 //
-// Kernel: one CTA per 128 x 128 output tile of one (modulus, digit group).
+// Kernel: persistent, one CTA per SM over the 128 x 128 output tiles of all
+// (modulus, digit group) pairs.
 //   warp 0: TMA producer (cp.async.bulk.tensor, SWIZZLE_128B, no multicast)
 //   warp 1: one thread issues tcgen05.mma (M = 128, N = 128, K = 32 bytes
-//           per instruction) into TMEM, tcgen05.commit frees smem stages
-//   warps 2-5: epilogue, tcgen05.ld 32x32b, combine, t_l = (C mod m) y mod m
+//           per instruction) into TMEM, tcgen05.commit frees smem stages and
+//           hands a finished accumulator to the epilogue
+//   warps 2-5: epilogue, tcgen05.ld 32x32b, combine, t_l = (C mod m) y mod m,
+//           then free the accumulator buffer for the MMA warp
 // Every mbarrier wait has an iteration limit; on expiry the CTA records
 // OZLU_ERR_TIMEOUT, stops issuing work, and releases its TMEM.
 #include <cuda.h>
@@ -124,36 +127,58 @@ __device__ __forceinline__ uint32_t t_value(int c, uint32_t m, uint32_t y, uint3
     return mod_small(r * y, m, magic);
 }
 
+// Persistent kernel: one CTA per SM walks the tiles (tm, tn, l, gi) with
+// stride gridDim.x, tn fastest, so the CTAs in flight share A row panels and
+// B column panels of one modulus in L2.  The smem ring runs across tiles; the
+// accumulators are double-buffered in TMEM (FP16: 2 x 128 columns; FP8 keeps
+// one 384-column buffer), so the epilogue of one tile overlaps the MMAs of
+// the next.
 template <bool FP8>
 __global__ void __launch_bounds__(THREADS, 1) gemm_tc05_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m, int n,
     int Mpad, int Npad, int KB, const __grid_constant__ DevTable tab, uint8_t* __restrict__ T,
     int* __restrict__ err) {
     constexpr int P = FP8 ? 3 : 1;                // planes (accumulators)
-    constexpr uint32_t TMEM_COLS = FP8 ? 512 : 128;
+    constexpr int NBUF = FP8 ? 1 : 2;             // accumulator buffers
+    constexpr uint32_t TMEM_COLS = FP8 ? 512 : 256;
     extern __shared__ uint8_t smem_raw[];
     uint8_t* sm = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sa = sm;
     uint8_t* sb = sm + STAGES * TILE;
     uint64_t* full = (uint64_t*)(sm + 2 * STAGES * TILE);
     uint64_t* empty = full + STAGES;
-    uint64_t* accb = empty + STAGES;
-    uint32_t* tmem_slot = (uint32_t*)(accb + 1);
+    uint64_t* accf = empty + STAGES;   // [NBUF] accumulator ready (MMA -> epilogue)
+    uint64_t* acce = accf + 2;         // [NBUF] accumulator free (epilogue -> MMA)
+    uint32_t* tmem_slot = (uint32_t*)(acce + 2);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tm = blockIdx.x, tn = blockIdx.y;
-    const int l = blockIdx.z % tab.N, gi = blockIdx.z / tab.N;
-    const int S = tab.S, g = tab.g0 + gi;
-    const int ta0 = max(0, g - (S - 1)), ta1 = min(g, S - 1);
-    const int items = (ta1 - ta0 + 1) * KB * P;
+    const int TM = Mpad / BM, TN = Npad / BN;
+    const int tiles = TM * TN * tab.N * tab.G;
+    const int S = tab.S;
+    // tile t -> (tm, tn, l, gi) and its work items (pair terms x K blocks x planes)
+    auto decode = [&](int t, int& tm, int& tn, int& l, int& gi, int& ta0, int& items) {
+        tn = t % TN;
+        int r = t / TN;
+        tm = r % TM;
+        r /= TM;
+        l = r % tab.N;
+        gi = r / tab.N;
+        const int g = tab.g0 + gi;
+        ta0 = max(0, g - (S - 1));
+        const int ta1 = min(g, S - 1);
+        items = (ta1 - ta0 + 1) * KB * P;
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accb, 1);
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(&accf[b], 1);
+            mbar_init(&acce[b], 128);
+        }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -170,26 +195,34 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc05_kernel(
 
     if (warp == 0) {
         if (lane == 0) {
-            int issued = 0;
-            for (int it = 0; it < items && !*abort; ++it) {
-                const int s = it % STAGES, round = it / STAGES;
-                if (!mbar_wait(&empty[s], (round & 1) ^ 1, err, abort)) break;
-                const int p = it % P, rest = it / P;
-                const int kb = rest % KB, pr = rest / KB;
-                const int ta = ta0 + pr, tb = g - ta;
-                mbar_expect_tx(&full[s], 2 * TILE);
-                const int ya = ((l * S + ta) * P + p) * Mpad + tm * BM;
-                const int yb = ((l * S + tb) * P + p) * Npad + tn * BN;
-                const int x = FP8 ? kb * BK : kb * (BK / 2);  // element units of the map
-                tma_load_2d(sa + s * TILE, &tmA, x, ya, &full[s]);
-                tma_load_2d(sb + s * TILE, &tmB, x, yb, &full[s]);
-                issued = it + 1;
+            long long it = 0;       // global item counter (smem ring position)
+            long long issued = 0;
+            for (int t = blockIdx.x; t < tiles && !*abort; t += gridDim.x) {
+                int tm, tn, l, gi, ta0, items;
+                decode(t, tm, tn, l, gi, ta0, items);
+                const int g = tab.g0 + gi;
+                for (int i = 0; i < items && !*abort; ++i, ++it) {
+                    const int s = (int)(it % STAGES);
+                    const long long round = it / STAGES;
+                    if (!mbar_wait(&empty[s], (uint32_t)((round & 1) ^ 1), err, abort)) break;
+                    const int p = i % P, rest = i / P;
+                    const int kb = rest % KB, pr = rest / KB;
+                    const int ta = ta0 + pr, tb = g - ta;
+                    mbar_expect_tx(&full[s], 2 * TILE);
+                    const int ya = ((l * S + ta) * P + p) * Mpad + tm * BM;
+                    const int yb = ((l * S + tb) * P + p) * Npad + tn * BN;
+                    const int x = FP8 ? kb * BK : kb * (BK / 2);  // element units of the map
+                    tma_load_2d(sa + s * TILE, &tmA, x, ya, &full[s]);
+                    tma_load_2d(sb + s * TILE, &tmB, x, yb, &full[s]);
+                    issued = it + 1;
+                }
             }
             if (*abort) {
                 // let the copies already issued land before the CTA exits (bounded)
-                for (int it = max(0, issued - STAGES); it < issued; ++it) {
+                for (long long q = issued - STAGES < 0 ? 0 : issued - STAGES; q < issued; ++q) {
                     long long w = 0;
-                    while (!mbar_try_wait(&full[it % STAGES], (it / STAGES) & 1) && ++w < WAIT_LIMIT) __nanosleep(64);
+                    while (!mbar_try_wait(&full[q % STAGES], (uint32_t)((q / STAGES) & 1)) && ++w < WAIT_LIMIT)
+                        __nanosleep(64);
                 }
             }
         }
@@ -198,30 +231,49 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc05_kernel(
             // kind::f8f6f4 E4M3 x E4M3 or kind::f16 F16 x F16 (format code 0 in both),
             // fp32 accumulate, K-major A and B, N = 128, M = 128
             const uint32_t idesc = (1u << 4) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
-            for (int it = 0; it < items; ++it) {
-                const int s = it % STAGES, round = it / STAGES;
-                if (!mbar_wait(&full[s], round & 1, err, abort)) break;
+            long long it = 0;
+            int j = 0;  // local tile count
+            for (int t = blockIdx.x; t < tiles && !*abort; t += gridDim.x, ++j) {
+                int tm, tn, l, gi, ta0, items;
+                decode(t, tm, tn, l, gi, ta0, items);
+                const int b = j % NBUF;
+                const uint32_t use = (uint32_t)(j / NBUF);
+                if (!mbar_wait(&acce[b], (use & 1) ^ 1, err, abort)) break;
                 asm volatile("tcgen05.fence::after_thread_sync;\n");
-                const int p = it % P;
-                const int first_of_plane = it < P;  // first item of each accumulator
-                const uint64_t ad = smem_desc(sa + s * TILE), bd = smem_desc(sb + s * TILE);
+                const uint32_t acc = tmem + (uint32_t)(b * P * BN);
+                bool ok = true;
+                for (int i = 0; i < items; ++i, ++it) {
+                    const int s = (int)(it % STAGES);
+                    const long long round = it / STAGES;
+                    if (!mbar_wait(&full[s], (uint32_t)(round & 1), err, abort)) { ok = false; break; }
+                    asm volatile("tcgen05.fence::after_thread_sync;\n");
+                    const int p = i % P;
+                    const int first_of_plane = i < P;  // first item of each accumulator
+                    const uint64_t ad = smem_desc(sa + s * TILE), bd = smem_desc(sb + s * TILE);
 #pragma unroll
-                for (int k = 0; k < BK / 32; ++k)
-                    mma<FP8>(tmem + p * BN, ad + 2 * k, bd + 2 * k, idesc, (first_of_plane && k == 0) ? 0u : 1u);
-                mma_commit(&empty[s]);
+                    for (int k = 0; k < BK / 32; ++k)
+                        mma<FP8>(acc + p * BN, ad + 2 * k, bd + 2 * k, idesc, (first_of_plane && k == 0) ? 0u : 1u);
+                    mma_commit(&empty[s]);
+                }
+                if (!ok) break;
+                mma_commit(&accf[b]);
             }
-            mma_commit(accb);
         }
     } else {
         // epilogue warps 2..5: TMEM lane quarter = warp % 4
         const int q = warp & 3;
-        const bool ok = mbar_wait(accb, 0, err, abort);
-        asm volatile("tcgen05.fence::after_thread_sync;\n");
-        if (ok) {
+        int j = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
+            int tm, tn, l, gi, ta0, items;
+            decode(t, tm, tn, l, gi, ta0, items);
+            const int b = j % NBUF;
+            const uint32_t use = (uint32_t)(j / NBUF);
+            if (!mbar_wait(&accf[b], use & 1, err, abort)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;\n");
             const uint32_t md = (uint32_t)tab.mod[l], yd = (uint32_t)tab.y[l], mg = tab.magic[l];
             const int i = tm * BM + q * 32 + lane;
             uint8_t* out = T + ((size_t)gi * tab.N + l) * (size_t)m * n;
-            const uint32_t lane_addr = tmem + ((uint32_t)(q * 32) << 16);
+            const uint32_t lane_addr = tmem + (uint32_t)(b * P * BN) + ((uint32_t)(q * 32) << 16);
             for (int ch = 0; ch < BN / 32; ++ch) {
                 uint32_t r0[32];
                 tmem_ld32(lane_addr + ch * 32, r0);
@@ -231,24 +283,27 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc05_kernel(
                     tmem_ld32(lane_addr + BN + ch * 32, r1);
                     tmem_ld32(lane_addr + 2 * BN + ch * 32, r2);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int p00 = (int)__uint_as_float(r0[j]);
-                        const int p11 = (int)__uint_as_float(r1[j]);
-                        const int pss = (int)__uint_as_float(r2[j]);
-                        c[j] = p00 + 17 * (pss - p00 - p11) + 289 * p11;
+                    for (int jj = 0; jj < 32; ++jj) {
+                        const int p00 = (int)__uint_as_float(r0[jj]);
+                        const int p11 = (int)__uint_as_float(r1[jj]);
+                        const int pss = (int)__uint_as_float(r2[jj]);
+                        c[jj] = p00 + 17 * (pss - p00 - p11) + 289 * p11;
                     }
                 } else {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) c[j] = (int)__uint_as_float(r0[j]);
+                    for (int jj = 0; jj < 32; ++jj) c[jj] = (int)__uint_as_float(r0[jj]);
                 }
                 if (i < m) {
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        const int col = tn * BN + ch * 32 + j;
-                        if (col < n) out[(size_t)col * m + i] = (uint8_t)t_value(c[j], md, yd, mg);
+                    for (int jj = 0; jj < 32; ++jj) {
+                        const int col = tn * BN + ch * 32 + jj;
+                        if (col < n) out[(size_t)col * m + i] = (uint8_t)t_value(c[jj], md, yd, mg);
                     }
                 }
             }
+            // the accumulator buffer may be overwritten by the next tile's MMAs
+            asm volatile("tcgen05.fence::before_thread_sync;\n");
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&acce[b])) : "memory");
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n");
@@ -288,7 +343,7 @@ bool make_map(CUtensorMap* tm, const void* base, bool fp8, int Kpad, long long r
 
 }  // namespace
 
-size_t tc05_smem_bytes() { return 2 * STAGES * TILE + 2 * STAGES * 8 + 8 + 16 + 1024; }
+size_t tc05_smem_bytes() { return 2 * STAGES * TILE + 2 * STAGES * 8 + 4 * 8 + 16 + 1024; }
 
 int launch_gemm_tc05(bool fp8, const void* RA, const void* RB, int m, int n, int Mpad, int Npad, int Kpad,
                      const DevTable& tab, uint8_t* T, int* err, cudaStream_t s) {
@@ -298,7 +353,14 @@ int launch_gemm_tc05(bool fp8, const void* RA, const void* RB, int m, int n, int
     if (!make_map(&tb, RB, fp8, Kpad, (long long)tab.N * tab.S * P * Npad)) return OZLU_ERR_UNSUPPORTED;
     const int KB = Kpad * (fp8 ? 1 : 2) / BK;
     const size_t smem = tc05_smem_bytes();
-    dim3 grid(Mpad / BM, Npad / BN, tab.N * tab.G);
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const long long tiles = (long long)(Mpad / BM) * (Npad / BN) * tab.N * tab.G;
+    dim3 grid((unsigned)(tiles < sms ? tiles : sms));
     if (fp8) {
         static bool set = false;
         if (!set) {
