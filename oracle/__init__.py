@@ -14,6 +14,7 @@ Modules
   plan       modulus set, CRT constants, the (S, w, N_mod) rule    Sec. 3.2
   expansion  exact values of DD/TD/QD expansions, RN to binary64   Sec. 2.1, 3.3
   oz2        Ozaki-II GEMM replay in exact integers (S1)-(S6)       Sec. 3.1-3.3
+  mp         the same replay for p-bit multi-limb numbers           Sec. 3.1, 3.4
   bigfloat   p-bit floating point with round-to-nearest-even        (LU at p+64)
   lu         exact rational LU, p-bit LU, solve, error measures     Sec. 3.4, 4.4
 
