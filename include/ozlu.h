@@ -234,6 +234,59 @@ int ozlu_gemm_noalloc(int nc, int p, int m, int n, int k, int alpha, const doubl
                       long long lda, const double* B, long long ldb, int beta, double* C,
                       long long ldc, void* stream);
 
+/*
+ * p-bit multi-limb matrices (the arbitrary-precision LU of Sec. 3.4 / 4.4,
+ * where the paper uses MPFR numbers).  Element (i, j) has a sign, an
+ * exponent and L 32-bit limbs of a magnitude normalised to its top bit:
+ *   value = (-1)^signs[x] * (sum_k limbs[k * plane + x] 2^(32 k)) * 2^(exps[x] - 32 L),
+ *   x = i + j * ld,
+ * so 2^(exps - 1) <= |value| < 2^exps; zero has all limbs 0 (exponent and
+ * sign 0).  Limb-major planes keep one limb of consecutive elements
+ * contiguous.  All three arrays are device memory owned by the caller; a
+ * submatrix is the same struct with the three pointers advanced by x.
+ * Results are rounded to p bits (round to nearest even), p <= 32 L.
+ */
+typedef struct {
+    unsigned int* limbs;
+    int* exps;
+    int* signs;
+    long long ld;     /* elements between columns, >= rows          */
+    long long plane;  /* elements between limb planes, >= ld * cols */
+    int L;            /* limbs per element                          */
+    int pad_;
+} ozlu_mp_matrix;
+
+/*
+ * C = beta * C + alpha * A * B on p-bit matrices by the Ozaki-II GEMM with
+ * INT8 residues (Sec. 3.1 (S1)-(S6) with p-bit significands in place of the
+ * expansions: S1 shared exponents, S2 trunc(a 2^mu) and S balanced digits,
+ * S3-S5 as for ozlu_gemm, S6 one rounding to p bits of beta C + alpha P_int
+ * with the old C truncated onto the product grid).
+ *   p >= 1; m, n >= 0; k >= 1; alpha +1 or -1; beta 0 or 1; C not aliased
+ *   with A or B; every matrix's L with 32 L >= p.
+ * The output is split into column chunks so that the t values of one chunk
+ * stay below 4 GiB.  Returns 0, -i for invalid argument i, or an OZLU_ERR_*
+ * code (OZLU_ERR_CAPACITY when no plan exists for p and k).
+ */
+int ozlu_mp_gemm(ozlu_handle* handle, int p, int m, int n, int k, int alpha, const ozlu_mp_matrix* A,
+                 const ozlu_mp_matrix* B, int beta, const ozlu_mp_matrix* C);
+
+/*
+ * LU with partial pivoting of an n x n p-bit matrix in place (Sec. 3.4): the
+ * recursive panel and triangular solves reduce to Ozaki-II GEMMs; a column
+ * of the panel takes a pivot search (largest |a|, lowest row on ties), a
+ * row interchange, and its scaling by the reciprocal of the pivot (Newton's
+ * iteration, Ozaki-II products of 1 x 1 operands).  ipiv (device, n ints,
+ * 1-based) and info (device int: 0, or the first exactly zero pivot) as in
+ * ozlu_getrf; nb = 0 picks 128.
+ */
+int ozlu_mp_getrf(ozlu_handle* handle, int p, int n, const ozlu_mp_matrix* A, int* ipiv, int nb,
+                  int* info);
+
+/* Solve A X = B from ozlu_mp_getrf's factors; B is n x nrhs (p-bit), overwritten. */
+int ozlu_mp_getrs(ozlu_handle* handle, int p, int n, int nrhs, const ozlu_mp_matrix* LU, const int* ipiv,
+                  const ozlu_mp_matrix* B);
+
 /* Version string of the library. */
 const char* ozlu_version(void);
 

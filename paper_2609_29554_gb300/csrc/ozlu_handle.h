@@ -81,6 +81,8 @@ int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, c
                 long long ldc, const ozlu_opts* opts);
 bool is_device_ptr(const void* p);
 int* err_word(ozlu_handle* h);
+int mp_gemm_device(ozlu_handle* h, int p, int m, int n, int k, int alpha, const ozlu_mp_matrix& A,
+                   const ozlu_mp_matrix& B, int beta, const ozlu_mp_matrix& C);
 int clear_err_word(ozlu_handle* h);
 int cuda_rc(cudaError_t e);
 }  // namespace ozlu

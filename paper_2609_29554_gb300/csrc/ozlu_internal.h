@@ -44,6 +44,7 @@ struct DevTable {
 };
 
 int make_plan(int p, int K, const ozlu_opts* o, Plan& out);
+int make_plan_mp(int p, int K, Plan& out);  // p-bit multi-limb inputs, INT8
 void fill_table(const Plan& pl, DevTable& t);
 
 // ---------------------------------------------------------------- kernels --

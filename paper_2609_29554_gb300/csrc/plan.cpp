@@ -151,6 +151,54 @@ int make_plan(int p, int K, const ozlu_opts* o, Plan& out) {
     return OZLU_ERR_CAPACITY;
 }
 
+// The same rule for p-bit multi-limb inputs (INT8 residues): S is not
+// bounded by the expansion kernels' fixed windows (S digits are produced one
+// at a time from the limbs and the CRT accumulates in a window sized from
+// the plan), only by the device tables (N_mod, words of S_g, 16-bit chunks
+// of a digit) and the INT32 accumulator condition.
+int make_plan_mp(int p, int K, Plan& out) {
+    if (p < 1 || K < 1) return OZLU_ERR_CAPACITY;
+    const int slack = ceil_log2(2.0 * K) + 16;
+    const int Kpad = (K + 127) / 128 * 128;
+    const std::vector<int> mods = int8_set();
+    for (int S = 1; S <= 4096; ++S) {
+        if ((double)Kpad * S * 127.0 * 127.0 >= ldexp(1.0, 31)) break;
+        const int w = (p + slack + S - 1) / S;
+        const double need = 2.0 * w + log2((double)K) + log2((double)S) + 5.0;
+        double cum = 0.0;
+        int N = 0;
+        for (int i = 0; i < (int)mods.size(); ++i) {
+            cum += log2((double)mods[i]);
+            if (cum > need) { N = i + 1; break; }
+        }
+        if (N == 0) continue;
+        Plan pl;
+        pl.p = p; pl.K = K; pl.Kpad = Kpad; pl.backend = OZLU_BE_INT8;
+        pl.S = S; pl.w = w; pl.Q = w * S; pl.N = N; pl.need = need;
+        pl.g0 = S - 1;
+        pl.G = S;
+        pl.pair_terms = 0;
+        for (int g = pl.g0; g <= 2 * S - 2; ++g) pl.pair_terms += std::min(g, 2 * S - 2 - g) + 1;
+        std::vector<uint32_t> P{1};
+        for (int i = 0; i < N; ++i) { pl.mod[i] = mods[i]; mul_small(P, (uint32_t)mods[i]); }
+        pl.P = P;
+        pl.M.resize(N);
+        for (int i = 0; i < N; ++i) {
+            pl.M[i] = div_small(P, (uint32_t)mods[i]);
+            pl.y[i] = inv_mod((int)mod_small(pl.M[i], (uint32_t)mods[i]), mods[i]);
+        }
+        pl.sbar_bits = 2 * w - 1 + ceil_log2((double)S * K) + 1;
+        pl.WG = (pl.sbar_bits + 31) / 32;
+        pl.pint_bits = w * (2 * S - 2 - pl.g0) + pl.sbar_bits;
+        pl.WX = 0;
+        pl.H = (w + 1 + 15) / 16;
+        if (N > MAXMOD || pl.WG > MAXWG || pl.H > MAXH) return OZLU_ERR_CAPACITY;
+        out = pl;
+        return OZLU_OK;
+    }
+    return OZLU_ERR_CAPACITY;
+}
+
 void fill_table(const Plan& pl, DevTable& t) {
     memset(&t, 0, sizeof t);
     t.N = pl.N; t.WG = pl.WG; t.H = pl.H; t.S = pl.S; t.w = pl.w; t.g0 = pl.g0;

@@ -57,6 +57,12 @@ class ozlu_stats(ctypes.Structure):
 _P = ctypes.c_void_p
 _I = ctypes.c_int
 _L = ctypes.c_longlong
+class ozlu_mp_matrix(ctypes.Structure):
+    _fields_ = [("limbs", ctypes.c_void_p), ("exps", ctypes.c_void_p), ("signs", ctypes.c_void_p),
+                ("ld", ctypes.c_longlong), ("plane", ctypes.c_longlong), ("L", ctypes.c_int),
+                ("pad_", ctypes.c_int)]
+
+
 SIGNATURES = {
     "ozlu_version": (ctypes.c_char_p, []),
     "ozlu_create": (_I, [ctypes.POINTER(_P), _P]),
@@ -73,6 +79,11 @@ SIGNATURES = {
     "ozlu_gemm_noalloc": (_I, [_I, _I, _I, _I, _I, _I, _P, _L, _P, _L, _I, _P, _L, _P]),
     "ozlu_getrf_batched": (_I, [_P, _I, _I, _I, _P, _P, _P, _P, _P, _I, ctypes.POINTER(ozlu_opts)]),
     "ozlu_getrs_batched": (_I, [_P, _I, _I, _I, _P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(ozlu_opts)]),
+    "ozlu_mp_gemm": (_I, [_P, _I, _I, _I, _I, _I, ctypes.POINTER(ozlu_mp_matrix),
+                          ctypes.POINTER(ozlu_mp_matrix), _I, ctypes.POINTER(ozlu_mp_matrix)]),
+    "ozlu_mp_getrf": (_I, [_P, _I, _I, ctypes.POINTER(ozlu_mp_matrix), _P, _I, _P]),
+    "ozlu_mp_getrs": (_I, [_P, _I, _I, _I, ctypes.POINTER(ozlu_mp_matrix), _P,
+                           ctypes.POINTER(ozlu_mp_matrix)]),
 }
 
 
@@ -225,3 +236,91 @@ def to_colmajor(X: np.ndarray) -> np.ndarray:
 def from_colmajor(Y: np.ndarray, rows: int) -> np.ndarray:
     """(cols, ld, nc) column-major -> (rows, cols, nc)."""
     return np.ascontiguousarray(np.transpose(Y[:, :rows, :], (1, 0, 2)))
+
+
+# ------------------------------------------------------------ p-bit matrices
+class MPMatrix:
+    """A rows x cols p-bit matrix in device memory, the layout of ozlu_mp_matrix.
+
+    Limb k of element (i, j) is limbs[k, i + j * rows] (int32 storage of the
+    32-bit words), with exps[i + j * rows] and signs[i + j * rows]; value =
+    (-1)^sign * mant * 2^(exp - 32 L) with mant normalised to its top bit.
+    """
+
+    def __init__(self, rows, cols, L, device="cuda"):
+        import torch
+        self.rows, self.cols, self.L = rows, cols, L
+        size = max(rows * cols, 1)
+        self.limbs = torch.zeros((L, size), dtype=torch.int32, device=device)
+        self.exps = torch.zeros(size, dtype=torch.int32, device=device)
+        self.signs = torch.zeros(size, dtype=torch.int32, device=device)
+
+    def desc(self, i0=0, j0=0):
+        """ozlu_mp_matrix of the submatrix with top-left (i0, j0)."""
+        off = i0 + j0 * self.rows
+        return ozlu_mp_matrix(self.limbs.data_ptr() + 4 * off, self.exps.data_ptr() + 4 * off,
+                              self.signs.data_ptr() + 4 * off, max(self.rows, 1),
+                              self.limbs.shape[1], self.L, 0)
+
+    @classmethod
+    def from_pairs(cls, pairs, L, device="cuda"):
+        """From rows of exact (N, E) pairs (value N 2^E, |N| < 2^(32 L))."""
+        import torch
+        rows, cols = len(pairs), len(pairs[0]) if pairs else 0
+        M = cls(rows, cols, L, device)
+        limbs = np.zeros((L, max(rows * cols, 1)), dtype=np.uint32)
+        exps = np.zeros(max(rows * cols, 1), dtype=np.int32)
+        signs = np.zeros(max(rows * cols, 1), dtype=np.int32)
+        for i in range(rows):
+            for j in range(cols):
+                N, E = pairs[i][j]
+                x = i + j * rows
+                if N == 0:
+                    continue
+                a = abs(int(N))
+                b = a.bit_length()
+                if b > 32 * L:
+                    raise ValueError("significand wider than 32 L bits")
+                mant = a << (32 * L - b)
+                for k in range(L):
+                    limbs[k, x] = (mant >> (32 * k)) & 0xffffffff
+                exps[x] = b + E
+                signs[x] = 1 if N < 0 else 0
+        M.limbs.copy_(torch.from_numpy(limbs.view(np.int32)))
+        M.exps.copy_(torch.from_numpy(exps))
+        M.signs.copy_(torch.from_numpy(signs))
+        return M
+
+    def to_pairs(self):
+        """Rows of exact (N, E) pairs (E = exp - 32 L)."""
+        limbs = self.limbs.cpu().numpy().view(np.uint32)
+        exps = self.exps.cpu().numpy()
+        signs = self.signs.cpu().numpy()
+        out = []
+        for i in range(self.rows):
+            row = []
+            for j in range(self.cols):
+                x = i + j * self.rows
+                mant = 0
+                for k in range(self.L - 1, -1, -1):
+                    mant = (mant << 32) | int(limbs[k, x])
+                if mant == 0:
+                    row.append((0, 0))
+                    continue
+                row.append((-mant if signs[x] else mant, int(exps[x]) - 32 * self.L))
+            out.append(row)
+        return out
+
+
+def ozlu_mp_gemm(h, p, m, n, k, alpha, A, B, beta, C):
+    """A, B, C: ozlu_mp_matrix descriptors (MPMatrix.desc())."""
+    _check("ozlu_mp_gemm", lib().ozlu_mp_gemm(h, p, m, n, k, alpha, ctypes.byref(A), ctypes.byref(B), beta,
+                                              ctypes.byref(C)))
+
+
+def ozlu_mp_getrf(h, p, n, A, ipiv, nb, info):
+    _check("ozlu_mp_getrf", lib().ozlu_mp_getrf(h, p, n, ctypes.byref(A), _ptr(ipiv), nb, _ptr(info)))
+
+
+def ozlu_mp_getrs(h, p, n, nrhs, LU, ipiv, B):
+    _check("ozlu_mp_getrs", lib().ozlu_mp_getrs(h, p, n, nrhs, ctypes.byref(LU), _ptr(ipiv), ctypes.byref(B)))
