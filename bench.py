@@ -18,6 +18,13 @@ A_i = U diag(sigma) V^T as above with one right-hand side b_i = A_i * ones
 ozlu_getrs_batched of fresh copies (CUDA graph replay after two warm-up
 calls).  Metric: sum_i 2 n_i^3 / 3 / t.
 
+--workload pbit: LU with partial pivoting of the Lotkin matrix (Sec. 4.4)
+stored as p-bit multi-limb numbers, p = 64 ceil(1.2 * 5.1 n / 64) (the
+paper's rule with log2 cond ~ 5.1 n; p = 12544 at n = 2048), nb = 256,
+ozlu_mp_getrf with INT8 residues; reports the solution error of A x = A 1
+and the split of the time into residue GEMMs, modular reduction + CRT and
+conversion.  Metric: (2 n^3 / 3) / t in p-bit Gflop/s.
+
 --impl reference times the CPU oracle (p + 64-bit LU, oracle/lu.py) on a
 bounded sample of the same workload (a smaller n of the same construction).
 Under torchrun each rank factors its own matrix (independent replicas,
@@ -46,8 +53,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ozlu", choices=["ozlu", "reference"])
-    ap.add_argument("--workload", default="lu", choices=["lu", "batched"])
-    ap.add_argument("--n", type=int, default=4096)
+    ap.add_argument("--workload", default="lu", choices=["lu", "batched", "pbit"])
+    ap.add_argument("--n", type=int, default=None, help="lu 4096, pbit 512")
     ap.add_argument("--nb", type=int, default=None, help="panel width (lu 256, batched 0 = library)")
     ap.add_argument("--nc", type=int, default=None, help="components (lu 4 = QD, batched 3 = TD)")
     ap.add_argument("--log10cond", type=float, default=40.0)
@@ -68,11 +75,159 @@ def parse():
                     help="oracle sample size (lu 352, batched 256)")
     a = ap.parse_args()
     lu = a.workload == "lu"
+    a.n = (512 if a.workload == "pbit" else 4096) if a.n is None else a.n
     a.nb = (256 if lu else 0) if a.nb is None else a.nb
     a.nc = (4 if lu else 3) if a.nc is None else a.nc
     a.seed = (4 if lu else 5) if a.seed is None else a.seed
     a.cpu_sample_n = (352 if lu else 256) if a.cpu_sample_n is None else a.cpu_sample_n
     return a
+
+
+def pbit_precision(n):
+    """p = 64 ceil(1.2 log2 cond / 64) with log2 cond(Lotkin_n) ~ 5.1 n."""
+    import math
+    return 64 * math.ceil(1.2 * 5.1 * n / 64)
+
+
+def lotkin_mp(n, p, L, ozlu, torch):
+    """The Lotkin matrix (row 0 ones, a_ij = 1/(i+j+1) below) as p-bit
+    numbers on the device, and b = A ones (rounded to p bits).
+
+    The entries depend on i + j only: the 2n distinct reciprocals are
+    correctly rounded on the host (integer division with a sticky bit) and
+    gathered on the device."""
+    import numpy as np
+
+    def rnd(num, den):
+        # correctly rounded num/den to p bits as (N, E)
+        k = p + 2 - (num.bit_length() - den.bit_length())
+        q, r = divmod(num << k, den) if k >= 0 else divmod(num, den << (-k))
+        q = (q << 1) | (1 if r else 0)
+        E = -k - 1
+        b = q.bit_length()
+        if b > p:
+            sh = b - p
+            low = q & ((1 << sh) - 1)
+            q >>= sh
+            half = 1 << (sh - 1)
+            if low > half or (low == half and (q & 1)):
+                q += 1
+            E += sh
+            if q.bit_length() > p:
+                q >>= 1
+                E += 1
+        return q, E
+
+    def enc(N, E):
+        b = N.bit_length()
+        mant = N << (32 * L - b)
+        return [(mant >> (32 * k)) & 0xffffffff for k in range(L)], b + E
+
+    table_l = np.zeros((L, 2 * n + 1), dtype=np.uint32)
+    table_e = np.zeros(2 * n + 1, dtype=np.int32)
+    for d in range(1, 2 * n + 1):
+        limbs, e = enc(*rnd(1, d))
+        table_l[:, d] = limbs
+        table_e[d] = e
+    ii = np.arange(n).reshape(n, 1)
+    jj = np.arange(n).reshape(1, n)
+    idx = np.where(ii == 0, 1, ii + jj + 1).T.reshape(-1)   # column-major; row 0: 1/1
+    M = ozlu.MPMatrix(n, n, L)
+    tl = torch.from_numpy(table_l.view(np.int32)).cuda()
+    te = torch.from_numpy(table_e).cuda()
+    ix = torch.from_numpy(idx.astype(np.int64)).cuda()
+    M.limbs.copy_(tl[:, ix])
+    M.exps.copy_(te[ix])
+    # b_i = sum_j a_ij: row 0 = n; row i = sum_{d=i+1}^{i+n} 1/d on a fixed-point grid of
+    # p + 64 + log2 n bits, then rounded to p bits (within 2^-(p+60) of the exact sum)
+    P = p + 64 + n.bit_length()
+    recips = [0] + [(1 << P) // d for d in range(1, 2 * n + 1)]
+    pref = np.cumsum(np.array([0] + recips[1:], dtype=object))
+    bpairs = []
+    for i in range(n):
+        if i == 0:
+            N, E = n, 0
+        else:
+            N, E = int(pref[i + n] - pref[i]), -P
+        bpairs.append([rnd(N, 1 << -E) if E < 0 else (N, E)])
+    return M, ozlu.MPMatrix.from_pairs(bpairs, L)
+
+
+def main_pbit(a, rank, world, local, ozlu, torch):
+    n = a.n
+    p = pbit_precision(n)
+    L = (p + 31) // 32
+    nb = a.nb or 256
+    t0 = time.perf_counter()
+    A0, b0 = lotkin_mp(n, p, L, ozlu, torch)
+    gen_s = time.perf_counter() - t0
+    A = ozlu.MPMatrix(n, n, L)
+    ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+    h = ozlu.ozlu_create(stream)
+
+    def step():
+        A.limbs.copy_(A0.limbs)
+        A.exps.copy_(A0.exps)
+        A.signs.copy_(A0.signs)
+        ozlu.ozlu_mp_getrf(h, p, n, A.desc(), ipiv, nb, info)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    ozlu.ozlu_set_timing(h, 1)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    with Clocks(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(a.steps):
+            step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier(world)
+    ms = ev0.elapsed_time(ev1) / a.steps
+    st = ozlu.ozlu_get_stats(h)
+    ozlu.ozlu_set_timing(h, 0)
+    ms_max = max_over_ranks(ms, world)
+    flops = 2.0 * n ** 3 / 3.0
+    value = job_value(flops, world, ms_max)
+    assert int(info.item()) == 0, "zero pivot in the Lotkin matrix"
+    # solve A x = b, correct bits of x against ones
+    x = ozlu.MPMatrix(n, 1, L)
+    x.limbs.copy_(b0.limbs)
+    x.exps.copy_(b0.exps)
+    x.signs.copy_(b0.signs)
+    ozlu.ozlu_mp_getrs(h, p, n, 1, A.desc(), ipiv, x.desc())
+    torch.cuda.synchronize()
+    from fractions import Fraction
+    import math
+    err = max(abs(Fraction(N) * Fraction(2) ** E - 1) for (N, E), in x.to_pairs())
+    # -log2 err without converting err to a float (it may be far below 2^-1074)
+    bits = (math.log2(err.denominator) - math.log2(err.numerator)) if err else float(p)
+    phases = {"gemm": st.gemm_ms, "crt": st.crt_ms, "convert": st.convert_ms,
+              "other": st.other_ms + st.panel_ms + st.trsm_ms}
+    achieved = st.gemm_ops / (st.gemm_ms * 1e-3) / 1e12 if st.gemm_ms else 0.0
+    rf = {"kernel": "gemm_imma_kernel", "bound": "tensor", "achieved": achieved, "peak": IMMA_PEAK,
+          "unit": "TOPS", "peak_source": "own mma.sync s8 probe", "frac": achieved / IMMA_PEAK,
+          "traffic": None, "phase_ms_per_step": {k: v / a.steps for k, v in phases.items()},
+          "note": "phase events over the timed steps (eager calls)"}
+    line = {"metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "u32 limbs (p-bit)", "data": "synthetic",
+            "config": {"workload": f"p-bit LU with partial pivoting of the Lotkin matrix, n = {n}, "
+                                   f"p = {p}, INT8 residues", "n": n, "p": p, "limbs": L, "nb": nb,
+                       "l2": "matrix copied in each step"},
+            "roofline": rf, "gpu_launches": int(st.launches), "clocks": clk.summary(),
+            "accuracy": {"solution_correct_bits": bits, "p_minus_log2cond_estimate": p - 5.1 * n,
+                         "how": "x of A x = A 1 against ones, b formed on a p + 64-bit grid"},
+            "setup_s": gen_s}
+    ozlu.ozlu_destroy(h)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
 
 
 def batched_sizes(a):
@@ -542,8 +697,8 @@ def main():
     torch.cuda.set_device(local)
     from paper_2609_29554_gb300 import build, ozlu
     build.build()
-    if a.workload == "batched":
-        rc = main_batched(a, rank, world, local, ozlu, torch)
+    if a.workload in ("batched", "pbit"):
+        rc = (main_batched if a.workload == "batched" else main_pbit)(a, rank, world, local, ozlu, torch)
         if world > 1:
             import torch.distributed as dist
             dist.destroy_process_group()

@@ -78,7 +78,8 @@ __device__ __forceinline__ int centered_residue(const uint32_t (&mag)[MAXD], boo
 // centered residues for every modulus, written to the int8 planes.
 //   A side (is_b = 0): element (r, h) of an R x K matrix, plane [l][t][r][h]
 //   B side (is_b = 1): element (h, r) of a K x R matrix, plane [l][t][r][h]
-// Threads cover the padded range [0, Rpad) x [0, Kpad) and write zeros there.
+// Threads cover [0, R) x [0, Kpad) and write zeros in the K padding; the
+// padded rows are left as they are (they only reach discarded outputs).
 // store residue r of plane (l, t) at element offset off, in the back-end's encoding
 // Residue modulo a binary64-back-end prime (m < 2^27): 64-bit sum of the
 // half products, then one 64-bit remainder.
@@ -126,10 +127,10 @@ __global__ void __launch_bounds__(256) convert_kernel(
     void* __restrict__ planes) {
     const int h = blockIdx.x * 32 + (threadIdx.x & 31);
     const int r = blockIdx.y * 8 + (threadIdx.x >> 5);
-    if (h >= Kpad || r >= Rpad) return;
+    if (h >= Kpad || r >= R) return;
     const size_t plane = (size_t)Rpad * Kpad;
     const size_t off = (size_t)r * Kpad + h;
-    if (r >= R || h >= K) {
+    if (h >= K) {
         for (int l = 0; l < tab.N; ++l)
             for (int t = 0; t < tab.S; ++t) put_residue<MODE>(planes, plane, l, tab.S, t, off, 0);
         return;
@@ -219,7 +220,10 @@ void launch_convert(const double* X, long long ld, int nc, int rows, int cols, b
     // A side: rows = R, cols = K; B side: rows = K, cols = R
     const int R = is_b ? cols : rows;
     const int K = is_b ? rows : cols;
-    dim3 grid((Kpad + 31) / 32, (Rpad + 7) / 8);
+    // rows [0, R) only: padded rows only feed padded output rows and columns,
+    // which the epilogue discards; the padded K columns must be zero
+    dim3 grid((Kpad + 31) / 32, (R + 7) / 8);
+    if (R == 0) return;
     switch (mode * 32 + tab.H) {
 #define OZLU_CONV(M, HH) \
     case M * 32 + HH: \

@@ -85,22 +85,22 @@ __device__ __forceinline__ int mp_residue(const uint32_t (&mag)[MPD], bool neg, 
 }
 
 // (S2)+(S3): one element per thread; A side: element (r, h), B side: (h, r);
-// planes [l][t][r][h] (Rpad x Kpad, zeros in the padding).  A threads run
-// along r (consecutive elements of a column), B threads along h.
+// planes [l][t][r][h] (Rpad x Kpad; zeros in the K padding, the padded rows
+// untouched).  A threads run along r (consecutive elements of a column), B
+// threads along h.
 template <int H>
 __global__ void __launch_bounds__(256) mp_convert_kernel(MPView X, int R, int Kc, int is_b,
                                                          const int* __restrict__ shifts,
                                                          const __grid_constant__ DevTable tab, int Kpad,
                                                          int Rpad, int8_t* __restrict__ planes) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    const long long total = (long long)Rpad * Kpad;
-    if (idx >= total) return;
-    const int r = is_b ? (int)(idx / Kpad) : (int)(idx % Rpad);
-    const int h = is_b ? (int)(idx % Kpad) : (int)(idx / Rpad);
-    const size_t plane = (size_t)total, off = (size_t)r * Kpad + h;
+    if (idx >= (long long)R * Kpad) return;
+    const int r = is_b ? (int)(idx / Kpad) : (int)(idx % R);
+    const int h = is_b ? (int)(idx % Kpad) : (int)(idx / R);
+    const size_t plane = (size_t)Rpad * Kpad, off = (size_t)r * Kpad + h;
     const int S = tab.S, w = tab.w;
     const long long x = is_b ? (long long)h + (long long)r * X.ld : (long long)r + (long long)h * X.ld;
-    if (r >= R || h >= Kc || mp_zero(X, x)) {
+    if (h >= Kc || mp_zero(X, x)) {
         for (int l = 0; l < tab.N; ++l)
             for (int t = 0; t < S; ++t) planes[(size_t)(l * S + t) * plane + off] = 0;
         return;
@@ -318,7 +318,9 @@ __global__ void __launch_bounds__(MPCT) mp_crt_kernel(const uint8_t* __restrict_
 template <int H>
 void convert_h(const MPView& X, int R, int Kc, int is_b, const int* shifts, const DevTable& tab, int Kpad, int Rpad,
                int8_t* planes, cudaStream_t s) {
-    const long long total = (long long)Rpad * Kpad;
+    // rows [0, R) only (padded rows reach discarded outputs); zeros in the K padding
+    const long long total = (long long)R * Kpad;
+    if (total == 0) return;
     mp_convert_kernel<H><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, R, Kc, is_b, shifts, tab, Kpad, Rpad,
                                                                          planes);
 }

@@ -5,9 +5,9 @@
 // arithmetic except the pivot search is Ozaki-II GEMMs (ozlu_mp_gemm):
 //   panel(r, b):  b = 1: pivot search (largest |a|, lowest row on ties), row
 //                 interchange across the outer panel, reciprocal of the pivot
-//                 by Newton's iteration x <- x (2 - a x) from a binary64
-//                 start (1 x 1 x 1 products at p + 32 bits), and the scaling
-//                 of the column below it (an m x 1 x 1 product);
+//                 (one block: Newton's iteration in fixed point from a
+//                 binary64 start), and the scaling of the column below it
+//                 (an m x 1 x 1 product);
 //                 else: panel(r, b/2), L11^-1 A12 on the right half, the
 //                 Schur update, panel(r + b/2, b - b/2)
 //   blocked over nb columns: panel, interchanges on the other columns,
@@ -122,25 +122,124 @@ __global__ void mp_laswp_kernel(MPV A, int k0, int k1, const int* ipiv, int j0, 
     }
 }
 
-// binary64 start of 1/a for element x of A into element 0 of R (53 bits of
-// significance, the rest of R's limbs zero), and the constant 2 into TWO
-__global__ void mp_recip_seed_kernel(MPV A, long long x, MPV R, MPV TWO) {
-    const uint64_t top = ((uint64_t)A.limbs[(long long)(A.L - 1) * A.plane + x] << 32) |
-                         (A.L > 1 ? A.limbs[(long long)(A.L - 2) * A.plane + x] : 0u);
-    // |a| = f 2^e with f = top / 2^64 in [1/2, 1); 1/|a| = (1/f) 2^-e
-    const double f = (double)(top >> 11) * 0x1p-53;
-    int ex;
-    const double fr = frexp(1.0 / f, &ex);  // 1/f = fr 2^ex, fr in [1/2, 1)
-    const uint64_t m53 = (uint64_t)ldexp(fr, 53);
-    for (int k = 0; k < R.L; ++k) R.limbs[(long long)k * R.plane] = 0;
-    R.limbs[(long long)(R.L - 1) * R.plane] = (uint32_t)(m53 >> 21);
-    if (R.L > 1) R.limbs[(long long)(R.L - 2) * R.plane] = (uint32_t)(m53 << 11);
-    R.exps[0] = ex - A.exps[x];
-    R.signs[0] = A.signs[x];
-    for (int k = 0; k < TWO.L; ++k) TWO.limbs[(long long)k * TWO.plane] = 0;
-    TWO.limbs[(long long)(TWO.L - 1) * TWO.plane] = 0x80000000u;
-    TWO.exps[0] = 2;
-    TWO.signs[0] = 0;
+// Block-cooperative fixed-point arithmetic for the reciprocal of one p-bit
+// number (one block of RT threads, words in shared memory).
+constexpr int RT = 256;
+
+// out[0, olen) = (X[0, nx) * Y[0, ny)) >> (32 shift), truncated: column sums
+// of the 32-bit halves of the limb products by all threads (64-bit, below
+// 2^(33 + log2 n)), then one thread propagates the carries
+__device__ void blk_mul(const uint32_t* X, int nx, const uint32_t* Y, int ny, uint32_t* out, int shift, int olen,
+                        unsigned long long* S) {
+    const int ncol = nx + ny;
+    for (int k = threadIdx.x; k < ncol; k += RT) {
+        unsigned long long acc = 0;
+        const int i0 = max(0, k - ny + 1), i1 = min(nx - 1, k);
+        for (int i = i0; i <= i1; ++i) acc += (uint32_t)((uint64_t)X[i] * Y[k - i]);
+        const int j0 = max(0, k - 1 - ny + 1), j1 = min(nx - 1, k - 1);
+        for (int i = j0; i <= j1; ++i) acc += (uint64_t)X[i] * Y[k - 1 - i] >> 32;
+        S[k] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long c = 0;
+        for (int k = 0; k < ncol; ++k) {
+            const unsigned long long v = S[k] + c;
+            if (k >= shift && k - shift < olen) out[k - shift] = (uint32_t)v;
+            c = v >> 32;
+        }
+        for (int k = ncol; k - shift < olen; ++k) {
+            if (k >= shift) out[k - shift] = (uint32_t)c;
+            c = 0;
+        }
+    }
+    __syncthreads();
+}
+
+// 1 / (element x of A) into element 0 of R (R.L limbs; truncated) by
+// Newton's iteration on the mantissa in fixed point: with f = |a| 2^-e in
+// [1/2, 1) (F = its L limbs) and y ~ 1/f (Y = y 2^(32 W), W = R.L):
+//   T = F Y 2^-(32 L) ~ f y 2^(32 W),  E = 2^(32 W) - T,  Y += Y E 2^-(32 W)
+// from a binary64 start; `iters` steps double the 53 correct bits each.
+__global__ void __launch_bounds__(RT) mp_recip_kernel(MPV A, long long x, MPV R, int iters) {
+    extern __shared__ unsigned long long rsm[];
+    const int La = A.L, W = R.L;
+    unsigned long long* S = rsm;                          // La + 2 W + 4 column sums
+    uint32_t* F = (uint32_t*)(S + La + 2 * W + 4);        // La
+    uint32_t* Y = F + La;                                 // W + 1
+    uint32_t* T = Y + W + 1;                              // W + 1
+    uint32_t* U = T + W + 1;                              // W + 1
+    for (int k = threadIdx.x; k < La; k += RT) F[k] = A.limbs[(long long)k * A.plane + x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint64_t top = ((uint64_t)F[La - 1] << 32) | (La > 1 ? F[La - 2] : 0u);
+        const double f = (double)(top >> 11) * 0x1p-53;
+        int ey;
+        const double fr = frexp(1.0 / f, &ey);         // 1/f = fr 2^ey, ey in {1, 2}
+        const uint64_t m53 = (uint64_t)ldexp(fr, 53);  // 1/f = m53 2^(ey - 53)
+        for (int k = 0; k <= W; ++k) Y[k] = 0;
+        const int pos = 32 * W + ey - 53;             // bit of Y holding m53's bit 0
+        const int q = pos >> 5, r = pos & 31;
+        Y[q] = (uint32_t)(m53 << r);
+        if (q + 1 <= W) Y[q + 1] = (uint32_t)(r ? (m53 >> (32 - r)) : (m53 >> 32));
+        if (q + 2 <= W && r) Y[q + 2] = (uint32_t)(m53 >> (64 - r));
+    }
+    __syncthreads();
+    for (int it = 0; it < iters; ++it) {
+        blk_mul(F, La, Y, W + 1, T, La, W + 1, S);      // T = F Y >> 32 La
+        if (threadIdx.x == 0) {
+            // E = 2^(32 W) - T (two's complement in W + 1 words), sign, |E| into T
+            uint64_t c = 1;
+            for (int k = 0; k <= W; ++k) {
+                const uint32_t o = k == W ? 1u : 0u;
+                const uint64_t v = (uint64_t)o + (uint32_t)~T[k] + c;
+                T[k] = (uint32_t)v;
+                c = v >> 32;
+            }
+            const bool eneg = (T[W] >> 31) != 0;
+            if (eneg) {
+                uint64_t c2 = 1;
+                for (int k = 0; k <= W; ++k) {
+                    const uint64_t v = (uint64_t)(uint32_t)~T[k] + c2;
+                    T[k] = (uint32_t)v;
+                    c2 = v >> 32;
+                }
+            }
+            U[0] = eneg ? 1u : 0u;  // sign, read below
+        }
+        __syncthreads();
+        const bool eneg = U[0] != 0;
+        __syncthreads();
+        blk_mul(Y, W + 1, T, W + 1, U, W, W + 1, S);     // U = Y |E| >> 32 W
+        if (threadIdx.x == 0) {
+            uint64_t c = eneg ? 1u : 0u;
+            for (int k = 0; k <= W; ++k) {
+                const uint32_t u = eneg ? ~U[k] : U[k];
+                const uint64_t v = (uint64_t)Y[k] + u + c;
+                Y[k] = (uint32_t)v;
+                c = v >> 32;
+            }
+        }
+        __syncthreads();
+    }
+    // normalise Y (value y 2^(32 W), y in (1, 2]) into R's W limbs, truncating
+    if (threadIdx.x == 0) {
+        int b = 0;
+        for (int k = W; k >= 0; --k)
+            if (Y[k]) {
+                b = 32 * k + 32 - __clz(Y[k]);
+                break;
+            }
+        const int first = b - 32 * W;  // Y bit at R's limb 0, bit 0
+        for (int k = 0; k < W; ++k) {
+            const int pos = first + 32 * k;
+            const int q = pos >> 5, r = pos & 31;
+            const uint32_t lo = (q >= 0 && q <= W) ? Y[q] : 0u, hi = (q + 1 >= 0 && q + 1 <= W) ? Y[q + 1] : 0u;
+            R.limbs[(long long)k * R.plane] = r ? (lo >> r) | (hi << (32 - r)) : lo;
+        }
+        R.exps[0] = b - 32 * W - A.exps[x];
+        R.signs[0] = A.signs[x];
+    }
 }
 
 // copy an m x n block (D, S with the same L)
@@ -205,22 +304,16 @@ struct Ctx {
     int rc = 0;
 };
 
-// 1 / M(i, j) into sc->x at p + 32 bits (Newton: y = 2 - a x, x = x y)
+// 1 / M(i, j) into sc->x (L + 1 limbs, correct to about p + 32 bits)
 int mp_reciprocal(Ctx& c, const ozlu_mp_matrix& M, long long i, long long j) {
-    cudaStream_t s = c.h->stream;
-    const int pp = c.p + 32;
-    Scratch& sc = *c.sc;
-    mp_recip_seed_kernel<<<1, 1, 0, s>>>(dv(M), i + j * M.ld, dv(sc.x), dv(sc.two));
+    const int W = c.sc->x.L, La = M.L;
+    int iters = 0;
+    for (int prec = 53; prec < c.p + 40; prec *= 2) ++iters;
+    const size_t smem = sizeof(unsigned long long) * (La + 2 * W + 4) + sizeof(uint32_t) * (La + 3 * (W + 1));
+    cudaFuncSetAttribute(mp_recip_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    mp_recip_kernel<<<1, RT, smem, c.h->stream>>>(dv(M), i + j * M.ld, dv(c.sc->x), iters);
     c.h->count(1);
-    int rc = 0;
-    for (int prec = 50; prec < pp + 8 && !rc; prec *= 2) {
-        mp_copy_kernel<<<1, 1, 0, s>>>(dv(sc.two), dv(sc.y), 1, 1);
-        c.h->count(1);
-        rc = mp_gemm_device(c.h, pp, 1, 1, 1, -1, sub(M, i, j), sc.x, 1, sc.y);
-        if (!rc) rc = mp_gemm_device(c.h, pp, 1, 1, 1, 1, sc.x, sc.y, 0, sc.z);
-        std::swap(sc.x, sc.z);
-    }
-    return rc;
+    return cudaGetLastError() == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
 }
 
 // rows [r0, r0 + m) x columns [j0, j0 + nc) of A scaled by sc->x (through

@@ -153,3 +153,21 @@ def test_mp_lu_singular():
     A = [[(1, i + j) for j in range(n)] for i in range(n)]
     h, dA, ipiv, info = factor(A, n, p, 4)
     assert info == 2
+
+
+@pytest.mark.parametrize("p", [128, 1024, 1600, 3136])
+def test_mp_reciprocal_through_1x1_solve(p):
+    """x = 1 / a from a 1 x 1 solve: the reciprocal kernel at p + 32 bits, then one
+    rounding to p bits (limb counts over one warp included)."""
+    rng = random.Random(p)
+    L = (p + 31) // 32
+    N = rng.getrandbits(p) | (1 << (p - 1))
+    A = ozlu.MPMatrix.from_pairs([[(N, -p + 3)]], L)
+    B = ozlu.MPMatrix.from_pairs([[(1, 0)]], L)
+    ipiv = torch.ones(1, dtype=torch.int32, device="cuda")
+    ozlu.ozlu_mp_getrs(handle(), p, 1, 1, A.desc(), ipiv, B.desc())
+    torch.cuda.synchronize()
+    (xn, xe), = B.to_pairs()[0]
+    ex = 1 / (Fraction(N) * Fraction(2) ** (-p + 3))
+    err = abs(Fraction(xn) * Fraction(2) ** xe - ex) / ex
+    assert err <= Fraction(2) ** (-p + 1)
