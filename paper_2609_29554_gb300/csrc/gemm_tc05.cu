@@ -19,7 +19,8 @@
 //   warp 1: one thread issues tcgen05.mma (M = 128, N = 128, K = 32 bytes
 //           per instruction) into TMEM, tcgen05.commit frees smem stages and
 //           hands a finished accumulator to the epilogue
-//   warps 2-5: epilogue, tcgen05.ld 32x32b, combine, t_l = (C mod m) y mod m,
+//   warps 2-9: epilogue (two warps per TMEM lane quarter, each on half of
+//           the columns), tcgen05.ld 32x32b, combine, t_l = (C mod m) y mod m,
 //           then free the accumulator buffer for the MMA warp
 // Every mbarrier wait has an iteration limit; on expiry the CTA records
 // OZLU_ERR_TIMEOUT, stops issuing work, and releases its TMEM.
@@ -34,7 +35,8 @@ namespace {
 
 constexpr int BM = 128, BN = 128, BK = 128;  // BK in bytes: one 128-byte swizzle row
 constexpr int STAGES = 6;
-constexpr int THREADS = 192;
+constexpr int THREADS = 320;  // producer, MMA, 8 epilogue warps
+constexpr int EPI = THREADS - 64;  // epilogue threads
 constexpr int TILE = BM * BK;                // 16 KiB per operand stage
 constexpr long long WAIT_LIMIT = 1ll << 24;  // iterations of ~100 ns
 
@@ -177,7 +179,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc05_kernel(
         }
         for (int b = 0; b < NBUF; ++b) {
             mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], 128);
+            mbar_init(&acce[b], EPI);
         }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -260,8 +262,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc05_kernel(
             }
         }
     } else {
-        // epilogue warps 2..5: TMEM lane quarter = warp % 4
+        // epilogue warps 2..9: TMEM lane quarter = warp % 4; warps 2-5 take the
+        // first half of the tile's columns, warps 6-9 the second
         const int q = warp & 3;
+        const int half = (warp - 2) >> 2;
         int j = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
             int tm, tn, l, gi, ta0, items;
@@ -274,7 +278,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc05_kernel(
             const int i = tm * BM + q * 32 + lane;
             uint8_t* out = T + ((size_t)gi * tab.N + l) * (size_t)m * n;
             const uint32_t lane_addr = tmem + (uint32_t)(b * P * BN) + ((uint32_t)(q * 32) << 16);
-            for (int ch = 0; ch < BN / 32; ++ch) {
+            for (int ch = half * (BN / 64); ch < (half + 1) * (BN / 64); ++ch) {
                 uint32_t r0[32];
                 tmem_ld32(lane_addr + ch * 32, r0);
                 int c[32];
