@@ -903,14 +903,15 @@ void trsm_base(const double* T, long long ldt, double* X, long long ldx, int b, 
 // rows does not fit in shared memory (the caller then uses column kernels).
 template <int N>
 bool base_block_coop(double* A, long long lda, int n, int c0, int b, int p0, int p1, int* ipiv,
-                     int* info, void* scratch, cudaStream_t s) {
+                     int* info, void* scratch, int min_rows, cudaStream_t s) {
     constexpr int L = Limbs<N>::L;
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // at least 16 rows per block: a small panel takes a few SMs and leaves the
-    // rest to concurrent work (the batched driver runs instances side by side)
-    const int g_rows = (n - c0 + 15) / 16;
+    // at least min_rows rows per block: a small panel takes a few SMs and
+    // leaves the rest to concurrent work (the batched driver runs instances
+    // side by side and asks for 32, single factorisations for 16)
+    const int g_rows = (n - c0 + min_rows - 1) / min_rows;
     for (int per_sm = 1; per_sm <= 2; ++per_sm) {
         int G = sms * per_sm;
         if (G > COOP_MAXG) G = COOP_MAXG;
@@ -1001,7 +1002,8 @@ void panel_rec(Ctx& c, int r, int b, int p0, int p1) {
     // in shared memory (else the block is split further)
     if (b <= coop_width(c, r)) {
         c.h->phase(PH_PANEL);
-        if (base_block_coop<N>(c.A, c.lda, c.n, r, b, p0, p1, c.ipiv, &c.sc->info, c.h->coop_scratch, s)) {
+        if (base_block_coop<N>(c.A, c.lda, c.n, r, b, p0, p1, c.ipiv, &c.sc->info, c.h->coop_scratch,
+                               c.h->coop_min_rows, s)) {
             c.h->count(1);
             c.h->stats.panel_launches += 1;
             return;

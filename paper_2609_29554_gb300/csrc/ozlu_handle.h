@@ -45,6 +45,7 @@ struct ozlu_handle {
     void* lu_scratch = nullptr;  // pivot-search scratch of ozlu_getrf
     void* coop_scratch = nullptr;  // grid-barrier and candidate slots of the panel kernel
     size_t coop_bytes = 0;
+    int coop_min_rows = 16;  // rows per block of the panel kernel at least (32 on batched sub-streams)
     // phase timing: (phase, start, end) event triples resolved in ozlu_get_stats
     std::vector<cudaEvent_t> pool;
     size_t pool_used = 0;
