@@ -629,7 +629,7 @@ def main_batched(a, rank, world, local, ozlu, torch):
     peaks, src = measured_peaks()
     rf = roofline(stp, a, peaks, src, fms=batched_fms(bt.ns), steps=1)
     rf["note"] = ("phase times of one eager pass with per-phase events, summed over the "
-                  "8 concurrent sub-streams")
+                  "concurrent sub-streams")
 
     line = {"metric": METRIC, "value": value, "unit": "Gflop/s", "n_gpus": world,
             "steps": a.steps, "warmup": max(a.warmup, 3), "ms_per_step": ms_max,

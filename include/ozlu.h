@@ -145,7 +145,7 @@ int ozlu_getrs(ozlu_handle* handle, int nc, int p, int n, int nrhs,
  *                     the 1-based column of the first exactly zero pivot), or
  *                     -OZLU_ERR_TIMEOUT when a bounded device wait gave up
  *   nb                panel width (0 = 128)
- * Instances run on up to 8 streams owned by the handle (joined back into the
+ * Instances run on up to 32 streams owned by the handle (joined back into the
  * handle's stream before return; the call does not wait for the GPU).  With
  * opts->graph the batch is captured into a CUDA graph on the second call with
  * the same sizes and pointers and replayed afterwards; the first call warms the

@@ -314,7 +314,7 @@ int ozlu_destroy(ozlu_handle* h) {
     for (auto& g : h->graphs)
         if (g.second.exec) cudaGraphExecDestroy(g.second.exec);
     h->graphs.clear();
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < MAX_SUB; ++k) {
         if (h->sub[k]) {
             cudaStream_t s = h->sub[k]->stream;
             ozlu_destroy(h->sub[k]);
@@ -343,7 +343,7 @@ int ozlu_set_stream(ozlu_handle* h, void* stream) {
 
 int ozlu_set_timing(ozlu_handle* h, int enable) {
     if (!h) return -1;
-    for (int k = 0; k < 8; ++k)
+    for (int k = 0; k < MAX_SUB; ++k)
         if (h->sub[k]) ozlu_set_timing(h->sub[k], enable);
     h->phase(-1);
     h->resolve_times();
@@ -360,7 +360,7 @@ int ozlu_get_stats(ozlu_handle* h, ozlu_stats* out) {
     h->phase(-1);
     h->resolve_times();
     *out = h->stats;
-    for (int k = 0; k < 8; ++k) {
+    for (int k = 0; k < MAX_SUB; ++k) {
         ozlu_handle* s = h->sub[k];
         if (!s) continue;
         s->phase(-1);

@@ -1,9 +1,9 @@
 // Batched LU and solve of many independent, unevenly sized instances.
 //
-// Instances are sorted by size and spread over up to 8 library-owned streams
+// Instances are sorted by size and spread over up to 32 library-owned streams
 // (greedy, by n^3), each with its own workspace, so that the latency-bound
 // panels of small instances run side by side: the cooperative panel kernel of
-// an instance takes about one SM per 16 rows.  Every residue GEMM of an
+// an instance takes about one SM per 32 rows.  Every residue GEMM of an
 // instance covers all moduli and digit groups in one launch.  With
 // opts->graph set, the whole batch (fork, per-stream instance sequences,
 // join) is captured into a CUDA graph on the second call with the same batch
@@ -22,7 +22,7 @@
 namespace ozlu {
 namespace {
 
-constexpr int NSUB = 8;
+constexpr int NSUB = MAX_SUB;
 
 int ensure_subs(ozlu_handle* h) {
     if (!h->fork && cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) != cudaSuccess) return OZLU_ERR_CUDA;

@@ -30,6 +30,8 @@ struct GemmLayout {
 
 }  // namespace ozlu
 
+constexpr int MAX_SUB = 32;  // library streams of the batched driver
+
 struct ozlu_handle {
     int device = 0;
     cudaStream_t stream = nullptr;
@@ -58,9 +60,9 @@ struct ozlu_handle {
     bool capturing = false;  // inside a CUDA-graph capture: no host synchronisation
     // batched driver: sub-handles with their own streams and workspaces, fork/join
     // events, and instantiated graphs keyed by the batch description
-    ozlu_handle* sub[8] = {};
+    ozlu_handle* sub[MAX_SUB] = {};
     cudaStream_t cap_stream = nullptr;  // graph captures run here
-    cudaEvent_t fork = nullptr, join[8] = {};
+    cudaEvent_t fork = nullptr, join[MAX_SUB] = {};
     struct Graph {
         cudaGraphExec_t exec;  // null: capture failed, the batch runs eagerly
         ozlu_stats work;       // counters of the captured call, added on each replay
