@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--compare", action="store_true",
                     help="also time the single-instance INT8 Ozaki-II LU and the native "
                          "(blocked-naive) expansion LU on the same matrix")
+    ap.add_argument("--eager", action="store_true",
+                    help="lu workload: launch every kernel directly instead of replaying a CUDA "
+                         "graph (a per-kernel profiler cannot replay the cooperative panel "
+                         "kernel inside a graph)")
     ap.add_argument("--no-accuracy", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -392,11 +396,16 @@ def run_reference(a):
 
 # ------------------------------------------------------------------ roofline --
 # Peaks for the integer and binary64 pipes come from this repository's own
-# probes on a GB300 (register-only loops, DESIGN.md): IMAD 18.9 T/s,
+# probes on a GB300 (register-only loops): IMAD 18.9 T/s,
 # mma.sync s8 151.6 TOPS.  Tensor-core peaks scale the measured bf16 number
 # by the nominal ratios (fp8 = 2x, fp16 = 1x).
 IMAD_PEAK = 18.9        # T IMAD/s
 IMMA_PEAK = 151.6       # TOPS (mma.sync s8)
+# DRAM bytes (read + write) per launch of the cooperative panel kernel, the
+# mean over the 32 base-block launches of one factorisation from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
+# (n, nc, nb, panel width)
+PANEL_TRAFFIC = {(4096, 4, 256, 0): 11.09e6}
 
 
 def roofline(st, a, peaks, src, fms=None, steps=None):
@@ -437,6 +446,10 @@ def roofline(st, a, peaks, src, fms=None, steps=None):
              "peak_source": "own IMAD probe"}
     r["frac"] = r["achieved"] / r["peak"]
     r["traffic"] = None
+    if dom == "panel" and a.workload == "lu":
+        r["traffic"] = PANEL_TRAFFIC.get((n, nc, a.nb, a.panel_width))
+        if r["traffic"] is not None:
+            r["traffic_source"] = "ncu capture of the same factorisation, bytes per launch"
     r["phase_ms_per_step"] = {k: v / steps for k, v in phases.items()}
     return r
 
@@ -713,7 +726,7 @@ def main():
     info = torch.zeros(1, dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
     h = ozlu.ozlu_create(stream)
-    opts = ozlu.make_opts(a.backend, graph=1, panel_width=a.panel_width)
+    opts = ozlu.make_opts(a.backend, graph=0 if a.eager else 1, panel_width=a.panel_width)
     flops = 2.0 * n ** 3 / 3.0
 
     def step():
@@ -740,7 +753,8 @@ def main():
     ms_max = max_over_ranks(ms, world)
     value = job_value(flops, world, ms_max)
     assert int(info.item()) == 0, "singular pivot or device timeout in the benchmark matrix"
-    assert st.graph_status == 2, f"expected CUDA graph replays (graph_status {st.graph_status})"
+    assert a.eager or st.graph_status == 2, \
+        f"expected CUDA graph replays (graph_status {st.graph_status})"
 
     # phase split: one eager pass with CUDA events around every phase (after
     # an untimed eager pass that warms this handle's workspace and autotuner;
@@ -763,7 +777,7 @@ def main():
             "data": "synthetic", "config": workload_config(a), "roofline": rf,
             "gpu_launches": int(st.launches), "clocks": clk.summary()}
     line["config"]["last_backend"] = {1: "int8", 2: "fp8", 3: "fp64", 4: "fp16"}.get(stp.last_backend)
-    line["config"]["launch"] = "CUDA graph replay of ozlu_getrf"
+    line["config"]["launch"] = ("eager launches" if a.eager else "CUDA graph replay") + " of ozlu_getrf"
 
     if not a.no_e2e:
         # the same LU through the public API from pinned host memory: the

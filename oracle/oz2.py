@@ -18,7 +18,7 @@ conversion of Sec. 3.3, in the paper's order and notation:
        a comparison with floor(P/2) for the sign
   (S6) c_bar = sum_g S_g 2^(wg), scaled by 2^-(mu_i+nu_j), rounded once.
 
-Readings (all listed in the design doc):
+Readings:
   * S1: E_i = max_h of the frexp exponent of the leading component a_ih[0], so
     |a_ih| < 2^E_i; mu_i = (Q-1) - E_i, hence |a_bar| < 2^(Q-1); an all-zero
     row gets mu_i = 0.

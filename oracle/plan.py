@@ -18,7 +18,7 @@ Paper passages followed:
   * Sec. 4.2.3, Eq. (14): binary16 residues (|r| <= 127) with an fp32
     accumulator need K_pad S 127^2 < 2^24; the INT8 modulus set is kept.
 
-Readings where the paper is silent or garbled (each listed in the design doc):
+Readings where the paper is silent or garbled:
   * the modulus order is descending (largest first); ascending order does not
     reproduce the printed GEMM counts, descending reproduces all of them;
   * the INT8 set uses 2^7 = 128 (|r| <= 127 for every modulus); the printed
