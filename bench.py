@@ -405,7 +405,7 @@ IMMA_PEAK = 151.6       # TOPS (mma.sync s8)
 # mean over the 32 base-block launches of one factorisation from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum), keyed by
 # (n, nc, nb, panel width)
-PANEL_TRAFFIC = {(4096, 4, 256, 0): 11.09e6}
+PANEL_TRAFFIC = {(4096, 4, 256, 0): 11.16e6}
 
 
 def roofline(st, a, peaks, src, fms=None, steps=None):

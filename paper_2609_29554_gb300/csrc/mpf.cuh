@@ -399,6 +399,10 @@ __device__ __forceinline__ MPF<L> add_windows(uint32_t (&X)[W], int ex, int xn, 
         A[i] = (uint32_t)s;
         brw = (s >> 63) & 1u;
     }
+    // a borrow out means A == B with the sticky set: the exact difference is
+    // below one unit of the window's last word (zero for an exact
+    // cancellation such as c = a b) and is returned as zero
+    if (brw) return mpf_make_zero<L>();
     return mpf_round<L, W>(A, ea, an, sticky);
 }
 
@@ -462,12 +466,18 @@ __device__ __forceinline__ MPF<L> mpf_from_double(double v) {
     return mpf_from_exp<L, 1>(&v);
 }
 
-// 1 / b by Newton's iteration r <- r (2 - f r) (quadratic convergence) on the
-// mantissa f = |b| 2^-e in [1/2, 1), from a double-double start: with
-// fh + fl the top 106 bits of f, r0 = 1 / fh (correctly rounded),
-// e = 1 - (fh + fl) r0 from two fused multiply-adds (the first is exact), and
-// r0 + r0 e is 1 / f to about 104 bits.  Steps double that until it covers
-// the 32 L bits of the format; the exponent is applied last, so no binary64
+// 1 / b on the mantissa f = |b| 2^-e in [1/2, 1), from a double-double start:
+// with fh + fl the top 106 bits of f, r0 = 1 / fh (correctly rounded),
+// d = 1 - (fh + fl) r0 from two fused multiply-adds (the first is exact), and
+// r = r0 + r0 d is 1 / f to about 103 bits.  Its residual e = 1 - f r (one
+// fused multiply-subtract, a single rounding) gives r = (1 - e) / f exactly, so
+//   r (1 + e)       = (1 - e^2) / f   (second order, about 206 bits),
+//   r (1 + e + e^2) = (1 - e^3) / f   (third order, about 309 bits),
+// each formed as r + r t by one more fused multiply-subtract.  e^2 (near
+// 2^-206) is wanted to about 50 bits only and is squared in binary64.  The
+// order is the lowest that covers the 32 L bits of the format (second for
+// L <= 6, third for L <= 9); longer formats continue with Newton steps
+// r <- r + r (1 - f r).  The exponent is applied last, so no binary64
 // quantity over- or underflows whatever the exponent of b.
 template <int L>
 __device__ __forceinline__ MPF<L> mpf_recip(const MPF<L>& b) {
@@ -475,18 +485,38 @@ __device__ __forceinline__ MPF<L> mpf_recip(const MPF<L>& b) {
     const uint64_t top = ((uint64_t)b.m[L - 1] << 32) | b.m[L - 2];
     const uint64_t nxt = ((uint64_t)b.m[L - 3] << 32) | b.m[L - 4];
     // f = m 2^(-32 L) ~ top 2^-64: fh = top[63:11] 2^-53, fl = the next 53 bits 2^-106
-    const double fh = scalbn((double)(top >> 11), -53);
-    const double fl = scalbn((double)(((top & 0x7ffull) << 42) | (nxt >> 22)), -106);
+    // (integers below 2^53 times powers of two: exact)
+    const double fh = (double)(top >> 11) * 0x1p-53;
+    const double fl = (double)(((top & 0x7ffull) << 42) | (nxt >> 22)) * 0x1p-106;
     const double r0 = 1.0 / fh;
-    double e = fma(-fh, r0, 1.0);
-    e = fma(-fl, r0, e);
-    const double seed[2] = {r0, r0 * e};
+    double d = fma(-fh, r0, 1.0);
+    d = fma(-fl, r0, d);
+    const double seed[2] = {r0, r0 * d};
     MPF<L> r = mpf_from_exp<L, 2>(seed);
     MPF<L> f = b;
     f.neg = 0;
     f.e = 0;
-    const MPF<L> two = mpf_from_double<L>(2.0);
-    for (int prec = 104; prec < 32 * L + 8; prec *= 2) r = mpf_mul<L>(r, mpf_sub<L>(two, mpf_mul<L>(f, r)));
+    MPF<L> one = mpf_make_zero<L>();
+    one.m[L - 1] = 0x80000000u;
+    one.e = 1;
+    MPF<L> e = mpf_fms<L>(one, f, r);
+    MPF<L> t = e;
+    int prec = 206;
+    if (32 * L + 8 > 206) {
+        // e^2 from the top 64 bits of e: |e| = m 2^(e.e - 32 L) ~ top64 2^(e.e - 64)
+        const int k = e.e - 64;
+        const double eh = (mpf_zero<L>(e) || k < -1000 || k > 1000)
+                              ? 0.0
+                              : (double)(((uint64_t)e.m[L - 1] << 32) | e.m[L - 2]) *
+                                    __longlong_as_double((long long)(k + 1023) << 52);
+        t = mpf_add<L>(e, mpf_from_double<L>(eh * eh));
+        prec = 309;
+    }
+    r = mpf_fms<L>(r, r, mpf_neg<L>(t));
+    for (; prec < 32 * L + 8; prec *= 2) {
+        e = mpf_fms<L>(one, f, r);
+        r = mpf_fms<L>(r, r, mpf_neg<L>(e));
+    }
     r.e -= b.e;
     r.neg = b.neg;
     return r;

@@ -137,6 +137,26 @@ def test_lotkin_dd_n128_nb32():
     assert r / scale < Fraction(2) ** -80
 
 
+@pytest.mark.parametrize("nc,n,nb", [(2, 40, 16), (3, 40, 32), (4, 40, 256)])
+def test_duplicate_rows_exact_cancellation(nc, n, nb):
+    # rows 3 and 7 are equal and hold the column-0 maximum 1.0 (reciprocal
+    # exactly 1): the first pivot is row 3, row 7 gets multiplier exactly 1
+    # and becomes exactly zero (a - 1 a = 0 in the fused multiply-subtract of
+    # the panel and in the Ozaki-II update), so every later pivot is nonzero
+    # except the last, an exact zero
+    A = random_expansions(n, n, nc, 9, -1, 1)
+    A[:, 0, :] *= 0.5
+    A[3, 0, :] = 0.0
+    A[3, 0, 0] = 1.0
+    A[7, :, :] = A[3, :, :]
+    dA, LU, ipiv, info = _getrf(A, nb)
+    assert info == n
+    assert np.all(LU[n - 1, n - 1] == 0.0)
+    assert np.all(np.isfinite(LU))
+    bits = _backward_error_bits(A, LU, ipiv)
+    assert bits < -53 * nc + 20, bits
+
+
 def test_singular_info():
     A = random_expansions(20, 20, 2, 3, -1, 1)
     A[:, 5, :] = 0.0
