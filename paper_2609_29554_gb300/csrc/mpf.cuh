@@ -466,56 +466,118 @@ __device__ __forceinline__ MPF<L> mpf_from_double(double v) {
     return mpf_from_exp<L, 1>(&v);
 }
 
-// 1 / b on the mantissa f = |b| 2^-e in [1/2, 1), from a double-double start:
-// with fh + fl the top 106 bits of f, r0 = 1 / fh (correctly rounded),
-// d = 1 - (fh + fl) r0 from two fused multiply-adds (the first is exact), and
-// r = r0 + r0 d is 1 / f to about 103 bits.  Its residual e = 1 - f r (one
-// fused multiply-subtract, a single rounding) gives r = (1 - e) / f exactly, so
-//   r (1 + e)       = (1 - e^2) / f   (second order, about 206 bits),
-//   r (1 + e + e^2) = (1 - e^3) / f   (third order, about 309 bits),
-// each formed as r + r t by one more fused multiply-subtract.  e^2 (near
-// 2^-206) is wanted to about 50 bits only and is squared in binary64.  The
-// order is the lowest that covers the 32 L bits of the format (second for
-// L <= 6, third for L <= 9); longer formats continue with Newton steps
-// r <- r + r (1 - f r).  The exponent is applied last, so no binary64
-// quantity over- or underflows whatever the exponent of b.
+template <int L>
+__device__ __forceinline__ MPF<L> mpf_one() {
+    MPF<L> r = mpf_make_zero<L>();
+    r.m[L - 1] = 0x80000000u;
+    r.e = 1;
+    return r;
+}
+
+// (top word of |a|)^2: a^2 to about 30 bits, positive (integer pipes only)
+template <int L>
+__device__ __forceinline__ MPF<L> mpf_top_square(const MPF<L>& a) {
+    MPF<L> r = mpf_make_zero<L>();
+    if (mpf_zero<L>(a)) return r;
+    // |a| ~ m_top 2^(a.e - 32), a^2 ~ q 2^(2 a.e - 64) with q = m_top^2 >= 2^62
+    uint64_t q = (uint64_t)a.m[L - 1] * a.m[L - 1];
+    int e = 2 * a.e;
+    if (!(q >> 63)) {
+        q <<= 1;
+        e -= 1;
+    }
+    r.m[L - 1] = (uint32_t)(q >> 32);
+    r.m[L - 2] = (uint32_t)q;
+    r.e = e;
+    return r;
+}
+
+// the same value with K < L words (low words zero)
+template <int L, int K>
+__device__ __forceinline__ MPF<L> mpf_widen(const MPF<K>& a) {
+    MPF<L> r;
+#pragma unroll
+    for (int i = 0; i < L - K; ++i) r.m[i] = 0;
+#pragma unroll
+    for (int i = 0; i < K; ++i) r.m[L - K + i] = a.m[i];
+    r.e = a.e;
+    r.neg = a.neg;
+    return r;
+}
+
+// 1 / f to about 60 bits for f = T 2^-64 + (lower bits) in [1/2, 1),
+// T in [2^63, 2^64): a binary32 reciprocal of the top 24 bits (relative error
+// below 2^-22), then two Newton steps r <- r + r e, e = 1 - T r 2^-64, in
+// 62-bit fixed point R = r 2^62 with 64 x 64-bit integer products (error
+// about 2^-44, then about 2^-61, the limit of R and of T).  No binary64.
+__device__ __forceinline__ MPF<4> mpf_recip_seed(uint64_t T) {
+    const float tf = (float)(uint32_t)(T >> 40);  // [2^23, 2^24), exact
+    const uint32_t bits = __float_as_uint(__frcp_rn(tf));
+    const int ex = (int)((bits >> 23) & 0xffu) - 127;  // 1 / tf in (2^-24, 2^-23]: -24 or -23
+    uint64_t R = (uint64_t)((bits & 0x7fffffu) | 0x800000u) << (ex + 63);
+#pragma unroll
+    for (int s = 0; s < 2; ++s) {
+        // E = 2^126 - T R (signed 128-bit), e = E 2^-126; |E| < 2^104, then < 2^82,
+        // so E >> sh fits in 63 bits
+        const uint64_t lo = T * R, hi = __umul64hi(T, R);
+        const uint64_t elo = 0ull - lo;
+        const uint64_t ehi = (1ull << 62) - hi - (lo != 0ull ? 1ull : 0ull);
+        const int sh = s == 0 ? 41 : 20;
+        const int64_t es = (int64_t)((ehi << (64 - sh)) | (elo >> sh));
+        // R e = R es 2^(sh - 126) = umulhi(R, |es|) 2^(sh - 62)
+        const uint64_t d = __umul64hi(R, es < 0 ? (uint64_t)(-es) : (uint64_t)es) >> (62 - sh);
+        R = es < 0 ? R - d : R + d;
+    }
+    // r = R 2^-62 as a 4-word float: R normalised into the top two words
+    const int z = __clzll((long long)R);
+    const uint64_t M = R << z;
+    MPF<4> r;
+    r.m[3] = (uint32_t)(M >> 32);
+    r.m[2] = (uint32_t)M;
+    r.m[1] = 0;
+    r.m[0] = 0;
+    r.e = 2 - z;
+    r.neg = 0;
+    return r;
+}
+
+// 1 / b on the mantissa f = |b| 2^-e in [1/2, 1), the exponent applied last.
+// From the seed r (above), the residual e = 1 - f r of one fused multiply-
+// subtract (a single rounding) gives r = (1 - e) / f exactly, so
+//   r (1 + e)       = (1 - e^2) / f   (second order),
+//   r (1 + e + e^2) = (1 - e^3) / f   (third order, e^2 from the top word of e),
+// each formed as r + r t by one more fused multiply-subtract.  A 4-word step
+// on the top 128 bits of f goes first (third order, about 180 bits, for
+// L = 4; second order, about 120 bits, otherwise), then one L-word step:
+// second order (about 240 bits) for L <= 6, third order (about 360 bits) for
+// L <= 11; longer formats continue with second-order steps.  Everything runs
+// on the integer pipes apart from one binary32 reciprocal.
 template <int L>
 __device__ __forceinline__ MPF<L> mpf_recip(const MPF<L>& b) {
-    static_assert(L >= 4, "double-double start needs 4 limbs");
-    const uint64_t top = ((uint64_t)b.m[L - 1] << 32) | b.m[L - 2];
-    const uint64_t nxt = ((uint64_t)b.m[L - 3] << 32) | b.m[L - 4];
-    // f = m 2^(-32 L) ~ top 2^-64: fh = top[63:11] 2^-53, fl = the next 53 bits 2^-106
-    // (integers below 2^53 times powers of two: exact)
-    const double fh = (double)(top >> 11) * 0x1p-53;
-    const double fl = (double)(((top & 0x7ffull) << 42) | (nxt >> 22)) * 0x1p-106;
-    const double r0 = 1.0 / fh;
-    double d = fma(-fh, r0, 1.0);
-    d = fma(-fl, r0, d);
-    const double seed[2] = {r0, r0 * d};
-    MPF<L> r = mpf_from_exp<L, 2>(seed);
-    MPF<L> f = b;
-    f.neg = 0;
-    f.e = 0;
-    MPF<L> one = mpf_make_zero<L>();
-    one.m[L - 1] = 0x80000000u;
-    one.e = 1;
-    MPF<L> e = mpf_fms<L>(one, f, r);
-    MPF<L> t = e;
-    int prec = 206;
-    if (32 * L + 8 > 206) {
-        // e^2 from the top 64 bits of e: |e| = m 2^(e.e - 32 L) ~ top64 2^(e.e - 64)
-        const int k = e.e - 64;
-        const double eh = (mpf_zero<L>(e) || k < -1000 || k > 1000)
-                              ? 0.0
-                              : (double)(((uint64_t)e.m[L - 1] << 32) | e.m[L - 2]) *
-                                    __longlong_as_double((long long)(k + 1023) << 52);
-        t = mpf_add<L>(e, mpf_from_double<L>(eh * eh));
-        prec = 309;
+    static_assert(L >= 4, "a 4-word first step");
+    MPF<4> r4 = mpf_recip_seed(((uint64_t)b.m[L - 1] << 32) | b.m[L - 2]);
+    MPF<4> f4;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) f4.m[i] = b.m[L - 4 + i];
+    f4.e = 0;
+    f4.neg = 0;
+    {
+        MPF<4> t4 = mpf_fms<4>(mpf_one<4>(), f4, r4);
+        if (L == 4) t4 = mpf_add<4>(t4, mpf_top_square<4>(t4));
+        r4 = mpf_fms<4>(r4, r4, mpf_neg<4>(t4));
     }
-    r = mpf_fms<L>(r, r, mpf_neg<L>(t));
-    for (; prec < 32 * L + 8; prec *= 2) {
-        e = mpf_fms<L>(one, f, r);
-        r = mpf_fms<L>(r, r, mpf_neg<L>(e));
+    MPF<L> r = mpf_widen<L, 4>(r4);
+    if (L > 4) {
+        MPF<L> f = b;
+        f.neg = 0;
+        f.e = 0;
+        MPF<L> t = mpf_fms<L>(mpf_one<L>(), f, r);
+        if (L > 6) t = mpf_add<L>(t, mpf_top_square<L>(t));
+        r = mpf_fms<L>(r, r, mpf_neg<L>(t));
+        for (int prec = L > 6 ? 360 : 240; prec < 32 * L + 8; prec *= 2) {
+            t = mpf_fms<L>(mpf_one<L>(), f, r);
+            r = mpf_fms<L>(r, r, mpf_neg<L>(t));
+        }
     }
     r.e -= b.e;
     r.neg = b.neg;

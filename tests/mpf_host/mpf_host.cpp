@@ -1,0 +1,94 @@
+// Host build of the device multi-limb float arithmetic (paper_2609_29554_gb300/csrc/mpf.cuh)
+// for CPU tests: the CUDA intrinsics it uses are given portable definitions
+// with the same results, the header is compiled as plain C++, and seeded
+// cases are printed for an exact check in Python.
+//
+// Output, one case per line: an op name, then each operand and the result as
+// "neg e m[L-1] ... m[0]" (words in hex), value = (-1)^neg m 2^(e - 32 L).
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <random>
+
+#define __device__
+#define __forceinline__ inline
+static inline int __clz(uint32_t x) { return x ? __builtin_clz(x) : 32; }
+static inline int __clzll(long long x) { return x ? __builtin_clzll((unsigned long long)x) : 64; }
+static inline long long __double_as_longlong(double d) { long long r; memcpy(&r, &d, 8); return r; }
+static inline double __longlong_as_double(long long x) { double r; memcpy(&r, &x, 8); return r; }
+static inline uint32_t __float_as_uint(float f) { uint32_t u; memcpy(&u, &f, 4); return u; }
+static inline float __frcp_rn(float x) { volatile float one = 1.0f; return one / x; }
+static inline uint32_t __umulhi(uint32_t a, uint32_t b) { return (uint32_t)(((uint64_t)a * b) >> 32); }
+static inline uint64_t __umul64hi(uint64_t a, uint64_t b) { return (uint64_t)(((unsigned __int128)a * b) >> 64); }
+static inline uint32_t __funnelshift_l(uint32_t lo, uint32_t hi, uint32_t s) {
+    s &= 31;
+    return s ? (hi << s) | (lo >> (32 - s)) : hi;
+}
+static inline uint32_t __funnelshift_r(uint32_t lo, uint32_t hi, uint32_t s) {
+    s &= 31;
+    return s ? (lo >> s) | (hi << (32 - s)) : lo;
+}
+
+#include "mpf.cuh"
+
+using namespace ozlu;
+
+template <int L>
+static void put(const MPF<L>& a) {
+    printf(" %d %d", a.neg, a.e);
+    for (int i = L - 1; i >= 0; --i) printf(" %08x", a.m[i]);
+}
+
+template <int L>
+static MPF<L> rnd(std::mt19937_64& g, int emin, int emax) {
+    MPF<L> v;
+    for (int i = 0; i < L; ++i) v.m[i] = (uint32_t)g();
+    v.m[L - 1] |= 0x80000000u;
+    v.e = emin + (int)(g() % (uint64_t)(emax - emin + 1));
+    v.neg = (int)(g() & 1);
+    return v;
+}
+
+template <int L>
+static void run(int n, uint64_t seed) {
+    std::mt19937_64 g(seed);
+    for (int i = 0; i < n; ++i) {
+        MPF<L> a = rnd<L>(g, -3, 3), b, c = rnd<L>(g, -6, 6);
+        const int kind = i % 8;
+        if (kind == 0) { b = a; b.m[0] ^= (uint32_t)g(); b.neg ^= 1; }                 // cancellation
+        else if (kind == 1) { b = a; b.neg ^= 1; }                                      // exact zero sum
+        else if (kind == 2) { b = a; b.m[L - 2] ^= 1u; b.neg ^= 1; }                    // deep cancellation
+        else if (kind == 3) { b = rnd<L>(g, -3 - 32 * (L + 3), 3); }                    // far apart
+        else if (kind == 4) { b = a; b.e -= 1 + (int)(g() % 70); }
+        else b = rnd<L>(g, -40, 40);
+        if (i % 97 == 0) b = mpf_make_zero<L>();
+        if (i % 5 == 0) { c = a; c.e = a.e + b.e; }                                      // c ~ a b
+        printf("mul %d", L); put<L>(a); put<L>(b); put<L>(mpf_mul<L>(a, b)); printf("\n");
+        printf("add %d", L); put<L>(a); put<L>(b); put<L>(mpf_add<L>(a, b)); printf("\n");
+        printf("fms %d", L); put<L>(c); put<L>(a); put<L>(b); put<L>(mpf_fms<L>(c, a, b)); printf("\n");
+        // exact cancellation: c = a b exactly (a, b with few significant bits)
+        if (i % 4 == 0) {
+            const double x = (double)(g() % 100000 + 1) * ((g() & 1) ? -1.0 : 1.0);
+            const double y = (double)(g() % 100000 + 1);
+            const MPF<L> xa = mpf_from_double<L>(x), yb = mpf_from_double<L>(y);
+            const MPF<L> cc = mpf_from_double<L>(x * y);
+            printf("fms %d", L); put<L>(cc); put<L>(xa); put<L>(yb); put<L>(mpf_fms<L>(cc, xa, yb)); printf("\n");
+        }
+        // reciprocal: random, f = 1/2, all-ones, a single low bit
+        MPF<L> r = rnd<L>(g, -2000, 2000);
+        if (i % 7 == 1) { for (int k = 0; k < L; ++k) r.m[k] = 0; r.m[L - 1] = 0x80000000u; }
+        if (i % 7 == 2) { for (int k = 0; k < L; ++k) r.m[k] = 0xffffffffu; }
+        if (i % 7 == 3) { for (int k = 0; k < L - 1; ++k) r.m[k] = 0; r.m[0] = 1u; r.m[L - 1] = 0x80000000u; }
+        printf("recip %d", L); put<L>(r); put<L>(mpf_recip<L>(r)); printf("\n");
+    }
+}
+
+int main(int argc, char** argv) {
+    const int n = argc > 1 ? atoi(argv[1]) : 1000;
+    run<4>(n, 1);
+    run<6>(n, 2);
+    run<8>(n, 3);
+    return 0;
+}
