@@ -157,6 +157,33 @@ def test_duplicate_rows_exact_cancellation(nc, n, nb):
     assert bits < -53 * nc + 20, bits
 
 
+@pytest.mark.parametrize("nc,n,nb", [(4, 96, 32), (3, 80, 16)])
+def test_schur_update_replay(nc, n, nb):
+    # per-step replay: from the GPU's factors, the first step's Schur update
+    # S = (P A)22 - L21 U12 (rows in the final pivot order, which commutes with
+    # the row-wise update) is recomputed by the GPU GEMM and by the oracle's
+    # Ozaki-II replay, bit for bit; the GPU's trailing factors L22 U22 then
+    # reproduce S to the backward-error bound of an LU
+    from oracle import oz2
+    from gpu_util import gpu_gemm
+    A = random_expansions(n, n, nc, 700 + n, -2, 2)
+    dA, LU, ipiv, info = _getrf(A, nb)
+    assert info == 0
+    PA = A.copy()
+    for k in range(n):
+        p = ipiv[k] - 1
+        PA[[k, p]] = PA[[p, k]]
+    L21 = np.ascontiguousarray(LU[nb:, :nb])
+    U12 = np.ascontiguousarray(LU[:nb, nb:])
+    C = np.ascontiguousarray(PA[nb:, nb:])
+    ref = oz2.oz2_gemm(L21, U12, 53 * nc, alpha=-1, beta=1, C=C)
+    got = gpu_gemm(L21, U12, alpha=-1, beta=1, C=C)
+    assert np.array_equal(got, ref)
+    m = n - nb
+    bits = _backward_error_bits(ref, np.ascontiguousarray(LU[nb:, nb:]), [k + 1 for k in range(m)])
+    assert bits < -53 * nc + math.log2(m) + 12, bits
+
+
 def test_singular_info():
     A = random_expansions(20, 20, 2, 3, -1, 1)
     A[:, 5, :] = 0.0
