@@ -85,10 +85,45 @@ static void run(int n, uint64_t seed) {
     }
 }
 
+// conversions between N-component binary64 expansions and L-word floats
+static double rnd_exp_component(std::mt19937_64& g, double prev) {
+    // below a quarter ulp of the previous component, random sign and size
+    const int e = std::ilogb(prev) - 54 - (int)(g() % 30);
+    const double m = 1.0 + (double)(g() >> 12) * 0x1p-52;
+    return ((g() & 1) ? -1.0 : 1.0) * std::ldexp(m, e);
+}
+
+template <int L, int N>
+static void run_conv(int n, uint64_t seed) {
+    std::mt19937_64 g(seed);
+    for (int i = 0; i < n; ++i) {
+        double x[N];
+        x[0] = ((g() & 1) ? -1.0 : 1.0) * std::ldexp(1.0 + (double)(g() >> 12) * 0x1p-52, (int)(g() % 81) - 40);
+        for (int c = 1; c < N; ++c) x[c] = rnd_exp_component(g, x[c - 1]);
+        if (i % 9 == 1) x[N - 1] = 0.0;                      // trailing zero component
+        if (i % 9 == 2) x[0] = std::ldexp(1.0, (int)(g() % 20));  // power-of-two leader
+        if (i % 9 == 3 && N > 2) { x[1] = 0.0; }              // interior zero
+        printf("fromexp %d %d", L, N);
+        for (int c = 0; c < N; ++c) printf(" %a", x[c]);
+        put<L>(mpf_from_exp<L, N>(x));
+        printf("\n");
+        const MPF<L> a = rnd<L>(g, -60, 60);
+        double out[N];
+        mpf_to_exp<L, N>(a, out);
+        printf("toexp %d %d", L, N);
+        put<L>(a);
+        for (int c = 0; c < N; ++c) printf(" %a", out[c]);
+        printf("\n");
+    }
+}
+
 int main(int argc, char** argv) {
     const int n = argc > 1 ? atoi(argv[1]) : 1000;
     run<4>(n, 1);
     run<6>(n, 2);
     run<8>(n, 3);
+    run_conv<4, 2>(n, 4);
+    run_conv<6, 3>(n, 5);
+    run_conv<8, 4>(n, 6);
     return 0;
 }

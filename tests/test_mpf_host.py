@@ -8,7 +8,10 @@ rational arithmetic:
   * mpf_fms (c - a b with one rounding): the same, including exact
     cancellations (c = a b gives zero);
   * mpf_recip: |1 - a r| < 2^-(32 L - 1) and the sign of a, for random,
-    f = 1/2, all-ones and single-low-bit mantissas over a wide exponent range.
+    f = 1/2, all-ones and single-low-bit mantissas over a wide exponent range;
+  * mpf_from_exp (N binary64 components, nonoverlapping, mixed signs, zero
+    components) rounds the exact sum to L words; mpf_to_exp gives the
+    successive round-to-nearest-even components x_c = RN(v - x_0 - ... - x_{c-1}).
 """
 import os
 import shutil
@@ -35,13 +38,22 @@ def cases(tmp_path_factory):
     for line in out.splitlines():
         t = line.split()
         op, L = t[0], int(t[1])
-        vals, k = [], 2
-        while k < len(t):
-            neg, e = int(t[k]), int(t[k + 1])
-            m = int("".join(t[k + 2:k + 2 + L]), 16)
-            vals.append((neg, e, m))
-            k += 2 + L
-        rows.append((op, L, vals))
+
+        def mpf(k):
+            return int(t[k]), int(t[k + 1]), int("".join(t[k + 2:k + 2 + L]), 16)
+
+        if op == "fromexp":        # L N x[0..N) result
+            N = int(t[2])
+            rows.append((op, L, ([float.fromhex(v) for v in t[3:3 + N]], mpf(3 + N))))
+        elif op == "toexp":        # L N a out[0..N)
+            N = int(t[2])
+            rows.append((op, L, (mpf(3), [float.fromhex(v) for v in t[5 + L:5 + L + N]])))
+        else:
+            vals, k = [], 2
+            while k < len(t):
+                vals.append(mpf(k))
+                k += 2 + L
+            rows.append((op, L, vals))
     return rows
 
 
@@ -118,4 +130,26 @@ def test_recip(cases):
         assert r[2] != 0 and r[0] == a[0]
         err = abs(1 - value(a, L) * value(r, L))
         assert err < Fraction(2) ** -(32 * L - 1), (L, float(err))
+    assert n >= 1800
+
+
+def test_from_expansion(cases):
+    n = bad = 0
+    for o, L, (x, r) in ((o, L, v) for o, L, v in cases if o == "fromexp"):
+        n += 1
+        exact = sum((Fraction(c) for c in x), Fraction(0))
+        bad += not same(r, rne(exact, L))
+    assert n >= 1800
+    assert bad == 0, f"{bad} of {n} conversions not correctly rounded"
+
+
+def test_to_expansion(cases):
+    n = 0
+    for o, L, (a, out) in ((o, L, v) for o, L, v in cases if o == "toexp"):
+        n += 1
+        rem = value(a, L)
+        for c in out:
+            want = float(rem)          # round to nearest even
+            assert c == want
+            rem -= Fraction(c)
     assert n >= 1800
