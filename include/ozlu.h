@@ -276,12 +276,21 @@ int ozlu_mp_gemm(ozlu_handle* handle, int p, int m, int n, int k, int alpha, con
  * recursive panel and triangular solves reduce to Ozaki-II GEMMs; a column
  * of the panel takes a pivot search (largest |a|, lowest row on ties), a
  * row interchange, and its scaling by the reciprocal of the pivot (Newton's
- * iteration, Ozaki-II products of 1 x 1 operands).  ipiv (device, n ints,
+ * iteration in fixed point by one thread block).  ipiv (device, n ints,
  * 1-based) and info (device int: 0, or the first exactly zero pivot) as in
  * ozlu_getrf; nb = 0 picks 128.
  */
 int ozlu_mp_getrf(ozlu_handle* handle, int p, int n, const ozlu_mp_matrix* A, int* ipiv, int nb,
                   int* info);
+
+/*
+ * The plan ozlu_mp_gemm uses for precision p and inner dimension k (Sec. 3.2
+ * "Determining w and N" with the 54 INT8 moduli: the smallest S whose width
+ * w = ceil((p + slack) / S) the moduli cover, within the INT32 accumulator
+ * bound).  Host only, no device work.  Returns 0, -i for invalid argument i,
+ * or OZLU_ERR_CAPACITY when no S satisfies both.
+ */
+int ozlu_mp_plan(int p, int k, ozlu_plan_info* out);
 
 /* Solve A X = B from ozlu_mp_getrf's factors; B is n x nrhs (p-bit), overwritten. */
 int ozlu_mp_getrs(ozlu_handle* handle, int p, int n, int nrhs, const ozlu_mp_matrix* LU, const int* ipiv,

@@ -235,3 +235,18 @@ extern "C" int ozlu_plan(int p, int k, const ozlu_opts* opts, ozlu_plan_info* ou
     for (int i = 0; i < pl.N && i < 64; ++i) out->moduli[i] = pl.mod[i];
     return OZLU_OK;
 }
+
+extern "C" int ozlu_mp_plan(int p, int k, ozlu_plan_info* out) {
+    if (p < 1) return -1;
+    if (k < 1) return -2;
+    if (!out) return -3;
+    ozlu::Plan pl;
+    int rc = ozlu::make_plan_mp(p, k, pl);
+    if (rc) return rc;
+    memset(out, 0, sizeof *out);
+    out->p = pl.p; out->K = pl.K; out->backend = pl.backend; out->S = pl.S; out->w = pl.w;
+    out->Q = pl.Q; out->n_mod = pl.N; out->g0 = pl.g0; out->n_groups = pl.G;
+    out->pair_terms = pl.pair_terms;
+    for (int i = 0; i < pl.N && i < 64; ++i) out->moduli[i] = pl.mod[i];
+    return OZLU_OK;
+}

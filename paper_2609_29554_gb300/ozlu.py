@@ -69,6 +69,7 @@ SIGNATURES = {
     "ozlu_destroy": (_I, [_P]),
     "ozlu_set_stream": (_I, [_P, _P]),
     "ozlu_plan": (_I, [_I, _I, ctypes.POINTER(ozlu_opts), ctypes.POINTER(ozlu_plan_info)]),
+    "ozlu_mp_plan": (_I, [_I, _I, ctypes.POINTER(ozlu_plan_info)]),
     "ozlu_gemm": (_I, [_P, _I, _I, _I, _I, _I, _I, _P, _L, _P, _L, _I, _P, _L,
                        ctypes.POINTER(ozlu_opts)]),
     "ozlu_getrf": (_I, [_P, _I, _I, _I, _P, _L, _P, _I, _P, ctypes.POINTER(ozlu_opts)]),
@@ -159,6 +160,12 @@ def ozlu_plan(p, k, opts=None):
     info = ozlu_plan_info()
     _check("ozlu_plan", lib().ozlu_plan(p, k, ctypes.byref(opts) if opts else None,
                                         ctypes.byref(info)))
+    return info
+
+
+def ozlu_mp_plan(p, k):
+    info = ozlu_plan_info()
+    _check("ozlu_mp_plan", lib().ozlu_mp_plan(p, k, ctypes.byref(info)))
     return info
 
 

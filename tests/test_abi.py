@@ -1,5 +1,6 @@
 """CPU checks of the C-ABI library: it builds, loads, exports every symbol
-include/ozlu.h declares, and its planner agrees with the oracle's plan."""
+include/ozlu.h declares, and its planners (expansion and p-bit) agree with the
+oracle's plan and with the counts the paper prints."""
 import os
 import re
 
@@ -44,12 +45,44 @@ def test_plan_matches_oracle(L, p, k, be, S, extra, gex):
     assert info.pair_terms == ref.pair_terms
 
 
+def _golden_int8_rows():
+    path = os.path.join(ROOT, "tests", "golden", "paper_counts.txt")
+    for line in open(path):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            be, p, K, S, N, ng = line.split()
+            if be == "int8" and S == "-":
+                yield int(p), int(K), None if N == "-" else int(N), None if ng == "-" else int(ng)
+
+
+@pytest.mark.parametrize("p,k,N,ng", list(_golden_int8_rows()) + [
+    (64, 1, None, None), (1100, 77, None, None), (3136, 256, None, None),
+    (6272, 256, None, None), (12544, 256, None, None)])
+def test_mp_plan_matches_oracle_and_paper(L, p, k, N, ng):
+    # the p-bit planner (ozlu_mp_gemm) on the paper's printed INT8 counts
+    # (Table gemmcount, the Sec. 4.2.6 table, Table backend_hp, the p = 8192
+    # text) and on the bench's Lotkin precisions
+    info = ozlu.ozlu_mp_plan(p, k)
+    ref = make_plan(p, k, backend="int8")
+    assert (info.S, info.w, info.Q, info.n_mod, info.g0) == (ref.S, ref.w, ref.Q, ref.N, ref.g0)
+    assert list(info.moduli)[:info.n_mod] == list(ref.moduli)
+    assert info.pair_terms == ref.pair_terms
+    if N is not None:
+        assert info.n_mod == N
+    if ng is not None:
+        assert info.pair_terms * info.n_mod == ng
+
+
 def test_bad_arguments_rejected(L):
     # argument checks happen before any device work
     rc = L.ozlu_gemm(None, 4, 0, 1, 1, 1, 1, None, 1, None, 1, 0, None, 1, None)
     assert rc == -1
     with pytest.raises(ozlu.OzluError):
         ozlu.ozlu_plan(0, 16)
+    with pytest.raises(ozlu.OzluError):
+        ozlu.ozlu_mp_plan(0, 16)
+    with pytest.raises(ozlu.OzluError):
+        ozlu.ozlu_mp_plan(128, 0)
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
