@@ -117,6 +117,32 @@ static void run_conv(int n, uint64_t seed) {
     }
 }
 
+// x mod m by one high multiply (mp_device.cuh mod_small, used for residues and
+// t values) against the % operator: every modulus m <= 255, x over edges and
+// a seeded sample of [0, 2^32)
+static void run_mod() {
+    std::mt19937_64 g(7);
+    long long n = 0, bad = 0;
+    for (uint32_t m = 2; m <= 255; ++m) {
+        const uint32_t magic = (uint32_t)(((1ull << 32) + m - 1) / m);
+        auto check = [&](uint32_t x) {
+            ++n;
+            bad += mod_small(x, m, magic) != x % m;
+        };
+        for (uint32_t x = 0; x < 4096; ++x) check(x);
+        for (uint32_t k = 1; k < 64; ++k) {
+            const uint64_t top = (1ull << 32) - 1;
+            check((uint32_t)(top - k));
+            const uint64_t mult = (top / m - k) * m;
+            check((uint32_t)mult);
+            check((uint32_t)(mult - 1));
+            check((uint32_t)(mult + 1));
+        }
+        for (int i = 0; i < 20000; ++i) check((uint32_t)g());
+    }
+    printf("mod %lld %lld\n", n, bad);
+}
+
 int main(int argc, char** argv) {
     const int n = argc > 1 ? atoi(argv[1]) : 1000;
     run<4>(n, 1);
@@ -125,5 +151,6 @@ int main(int argc, char** argv) {
     run_conv<4, 2>(n, 4);
     run_conv<6, 3>(n, 5);
     run_conv<8, 4>(n, 6);
+    run_mod();
     return 0;
 }

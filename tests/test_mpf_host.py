@@ -11,7 +11,10 @@ rational arithmetic:
     f = 1/2, all-ones and single-low-bit mantissas over a wide exponent range;
   * mpf_from_exp (N binary64 components, nonoverlapping, mixed signs, zero
     components) rounds the exact sum to L words; mpf_to_exp gives the
-    successive round-to-nearest-even components x_c = RN(v - x_0 - ... - x_{c-1}).
+    successive round-to-nearest-even components x_c = RN(v - x_0 - ... - x_{c-1});
+  * mod_small (x mod m by one high multiply, used for every residue and t
+    value) equals x % m for every m <= 255 over edge values and a sample of
+    [0, 2^32).
 """
 import os
 import shutil
@@ -37,11 +40,14 @@ def cases(tmp_path_factory):
     rows = []
     for line in out.splitlines():
         t = line.split()
-        op, L = t[0], int(t[1])
+        op, L = t[0], int(t[1]) if t[0] != "mod" else 0
 
         def mpf(k):
             return int(t[k]), int(t[k + 1]), int("".join(t[k + 2:k + 2 + L]), 16)
 
+        if op == "mod":            # cases mismatches
+            rows.append((op, 0, (int(t[1]), int(t[2]))))
+            continue
         if op == "fromexp":        # L N x[0..N) result
             N = int(t[2])
             rows.append((op, L, ([float.fromhex(v) for v in t[3:3 + N]], mpf(3 + N))))
@@ -153,3 +159,8 @@ def test_to_expansion(cases):
             assert c == want
             rem -= Fraction(c)
     assert n >= 1800
+
+
+def test_mod_small(cases):
+    (n, bad), = [v for o, L, v in cases if o == "mod"]
+    assert n > 5_000_000 and bad == 0
