@@ -1,7 +1,8 @@
 // Device arithmetic on non-overlapping expansions of N binary64 components
 // (DD N = 2, TD N = 3, QD N = 4; Sec. 2.1), built from the error-free
-// transformations TwoSum and TwoProd (FMA).  Used by the panel (P1), the
-// triangular solves (P3, getrs) and the native per-element LU baseline.
+// transformations TwoSum and TwoProd (FMA).  Used by the panel's column
+// kernels where the cooperative base-block kernel does not apply (its rows do
+// not fit in shared memory) and by the native per-element LU baseline.
 //
 // Products and sums are formed order by order: terms of order k (about
 // 2^(-53 k) relative to the leading one) are added with TwoSum, each rounding
