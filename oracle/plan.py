@@ -17,6 +17,13 @@ Paper passages followed:
   * Sec. 4.2.3, Eq. (15): FP8 balanced base-17 digits keep the INT8 set.
   * Sec. 4.2.3, Eq. (14): binary16 residues (|r| <= 127) with an fp32
     accumulator need K_pad S 127^2 < 2^24; the INT8 modulus set is kept.
+  * Sec. 4.2.4 "Precision ceiling of the INT8 back-end": moduli above 255
+    (up to 16257, Eq. (int8lim)) with the centered residue split into two
+    balanced base-128 digits r = 128 q + r0 and the product formed by
+    Karatsuba from the three int8 planes r0, r0 + q, q; the table holds about
+    1880 pairwise-coprime moduli not exceeding 16191, 23226 bits.
+  * Sec. 3.2 "Choosing S: a cost model", Eq. (Lhint):
+    S* = ceil(sqrt(r n_d (M + N) / (M N))), n_d = ceil(t / 16).
 
 Readings where the paper is silent or garbled:
   * the modulus order is descending (largest first); ascending order does not
@@ -27,6 +34,11 @@ Readings where the paper is silent or garbled:
     smallest S whose modulus set has enough capacity, subject to the
     accumulator condition;
   * K_pad is K rounded up to a multiple of 128.
+  * The extended table is the 54 INT8 moduli together with the primes in
+    (255, 16191]: 1882 moduli and 23226.2 bits, the two figures the paper
+    prints; it is taken in descending order like the INT8 set, and every
+    modulus above 255 costs three int8 GEMMs (its Karatsuba planes).
+  * In Eq. (Lhint), t is the width of one unsplit pass, p + slack.
 """
 from __future__ import annotations
 
@@ -75,6 +87,41 @@ def fp64_moduli(K: int) -> list[int]:
     return primes_upto(bound)[::-1]
 
 
+EXT_LIMIT = 16191      # Sec. 4.2.4: the extended table's largest entry bound
+EXT_MAX_MODULUS = 16257  # Eq. (int8lim): |r| <= 63 * 128 + 64 = 8128
+
+
+def ext_moduli() -> list[int]:
+    """Extended INT8 table (Sec. 4.2.4): the 54 INT8 moduli and the primes in
+    (255, 16191], pairwise coprime, largest first."""
+    big = [q for q in primes_upto(EXT_LIMIT) if q > 255]
+    return sorted(int8_moduli() + big, reverse=True)
+
+
+def base128_digits(r: int) -> tuple[int, int]:
+    """r = 128 q + r0 with |r0| <= 64 (Sec. 4.2.4); q is the nearest integer to
+    r / 128, ties toward zero (so r0 = +-64 keeps the sign of r).  For
+    |r| <= 8128, |q| <= 63 and |r0 + q| <= 127, so all three Karatsuba planes
+    are int8."""
+    q = (abs(r) + 63) // 128
+    if r < 0:
+        q = -q
+    return r - 128 * q, q
+
+
+def residue_planes(m: int) -> int:
+    """int8 GEMMs per modulus: 1 up to 255, 3 (Karatsuba) above."""
+    return 1 if m <= 255 else 3
+
+
+def lhint_S(r: float, t: int, M: int, N: int) -> int:
+    """Eq. (Lhint): the cost-model estimate S* = ceil(sqrt(r n_d (M+N)/(MN))),
+    n_d = ceil(t/16); r = 30 (INT8) or 17.9 (binary64) as calibrated in the
+    paper, t the width of one unsplit pass."""
+    n_d = -(-t // 16)
+    return max(1, math.ceil(math.sqrt(r * n_d * (M + N) / (M * N))))
+
+
 def pairs_in_group(g: int, S: int) -> int:
     """Number of (ta, tb) with ta + tb = g, 0 <= ta, tb < S (Sec. 3.2)."""
     return min(g, 2 * S - 2 - g) + 1
@@ -102,6 +149,7 @@ class Plan:
     M: tuple = field(repr=False)
     y: tuple = field(repr=False)
     g0: int = 0
+    modset: str = "int8"
 
     @property
     def groups(self) -> range:
@@ -114,8 +162,11 @@ class Plan:
 
     @property
     def n_gemm(self) -> int:
-        """#GEMM = S(S+1)/2 * N_mod with no extra groups (Eq. (8))."""
-        return self.pair_terms * self.N
+        """#GEMM = S(S+1)/2 * N_mod with no extra groups (Eq. (8)); a modulus
+        of the extended table above 255 counts its three Karatsuba planes."""
+        if self.modset != "ext":
+            return self.pair_terms * self.N
+        return self.pair_terms * sum(residue_planes(m) for m in self.moduli)
 
 
 def _accumulator_ok(backend: str, K: int, S: int) -> bool:
@@ -134,15 +185,22 @@ def _accumulator_ok(backend: str, K: int, S: int) -> bool:
 
 def make_plan(p: int, K: int, backend: str = "int8", g_ex: int = 0,
               extra_groups: int = 0, S: int | None = None,
-              use_256: bool = False) -> Plan:
-    """The (S, w, Q, N_mod) rule of Sec. 3.2 "Determining w and N"."""
+              use_256: bool = False, modset: str = "int8") -> Plan:
+    """The (S, w, Q, N_mod) rule of Sec. 3.2 "Determining w and N".
+
+    modset "ext" (INT8 back-end only) takes the moduli from the extended
+    table of Sec. 4.2.4 instead of the 54 moduli up to 255."""
     if p < 1 or K < 1:
         raise ValueError("p and K must be positive")
+    if modset not in ("int8", "ext") or (modset == "ext" and backend != "int8"):
+        raise ValueError("the extended table is an INT8 route")
     slack = math.ceil(math.log2(2 * K)) + 16 + g_ex
     s_range = [S] if S is not None else range(1, 4097)
     for s in s_range:
         if backend == "fp64":
             mods = fp64_moduli(K)
+        elif modset == "ext":
+            mods = ext_moduli()
         else:
             mods = int8_moduli(use_256)
         if not _accumulator_ok(backend, K, s):
@@ -166,7 +224,7 @@ def make_plan(p: int, K: int, backend: str = "int8", g_ex: int = 0,
         return Plan(p=p, K=K, backend=backend, g_ex=g_ex,
                     extra_groups=extra_groups, slack=slack, S=s, w=w,
                     Q=w * s, need=need, N=n_mod, moduli=chosen, P=P, M=M,
-                    y=y, g0=g0)
+                    y=y, g0=g0, modset=modset)
     raise ValueError(f"no plan for p={p} K={K} backend={backend}")
 
 

@@ -212,3 +212,75 @@ def test_zero_rows_and_columns():
     B[:, 2] = 0.0
     out = oz2.oz2_gemm(A, B, 106)
     assert np.all(out[1] == 0.0) and np.all(out[:, 2] == 0.0)
+
+
+def test_window_raise_keeps_far_c_unchanged():
+    # (S6) with beta = 1 and an old C far above the product: the grid is
+    # raised (e_top - E0 > WINDOW_BITS) and the result must be C itself, since
+    # the product lies below half a unit of C's last component
+    A, B = _rand(3, 6, 2, 4, 501, -2, 2)
+    C = random_expansions(3, 2, 4, 502, 600, 620)
+    out, d = oz2.oz2_gemm(A, B, 212, alpha=-1, beta=1, C=C, debug=True)
+    for i in range(3):
+        for j in range(2):
+            E0 = d.plan.w * d.plan.g0 - d.mu[i] - d.nu[j]
+            e_top = max(E0 + abs(int(d.Pint[i, j])).bit_length(), math.frexp(C[i, j, 0])[1]) + 1
+            assert e_top - E0 > oz2.WINDOW_BITS       # the raise is exercised
+            assert list(out[i, j]) == list(C[i, j])
+
+
+def test_window_raise_within_bound_on_sparse_c():
+    # a sparse old C whose low component falls below the raised grid: the
+    # single rounding stays within one unit 2^-p of the exact beta C + alpha A B
+    A, B = _rand(2, 4, 2, 4, 511, -1, 1)
+    C = np.zeros((2, 2, 4))
+    C[..., 0] = 2.0 ** 600
+    C[..., 1] = 2.0 ** 60
+    out = oz2.oz2_gemm(A, B, 212, alpha=1, beta=1, C=C)
+    ex = _exact(A, B)
+    for i in range(2):
+        for j in range(2):
+            ref = expansion_value(C[i, j]) + ex[i][j]
+            assert abs(expansion_value(out[i, j]) - ref) <= ulp_p(ref, 212)
+
+
+def test_gamma_factor_closed_form():
+    # Eq. (7): a = [1, 1], b = [1, -1 + 2^-k]: c = 2^-k, max|a| max|b| = 1,
+    # so Gamma = 2^k exactly
+    for k in (1, 40, 150):
+        A = np.zeros((1, 2, 4))
+        A[0, :, 0] = 1.0
+        B = np.zeros((2, 1, 4))
+        B[0, 0, 0] = 1.0
+        B[1, 0, 0], B[1, 0, 1] = -1.0, 2.0 ** -k
+        if k < 53:
+            B[1, 0, :] = 0.0
+            B[1, 0, 0] = -1.0 + 2.0 ** -k
+        g = oz2.gamma_factor(A, B)
+        assert g[0, 0] == 2.0 ** k
+
+
+def test_gamma_guard_of_proposition2():
+    # Prop. 2 / Eq. (6): the result is within the unit 2^-p of c once Q covers
+    # p + log2 Gamma + log2 2K + log2 S + g0, i.e. with g_ex >= log2 Gamma; with
+    # no guard the dropped digit group shows at about Gamma 2^-Q relative
+    rng = np.random.default_rng(77)
+    A, Bh = _rand(1, 1, 1, 4, 91, 0, 0)
+    A = np.concatenate([A, A], axis=1)                    # row [a, a]
+    B = np.zeros((2, 1, 4))
+    B[0, 0] = Bh[0, 0]                                    # b, all four components
+    neg = -Bh[0, 0]
+    B[1, 0, 0], B[1, 0, 1] = neg[0], neg[1]               # -b + delta: keep the top two
+    B[1, 0, 2] = 2.0 ** -120 * (1 + rng.random())         # delta far below b
+    gam = float(oz2.gamma_factor(A, B)[0, 0])
+    k = math.ceil(math.log2(gam))
+    assert 100 <= k <= 130
+    ex = _exact(A, B)[0][0]
+    err = {}
+    for gex in (0, k):
+        plan = make_plan(212, 2, g_ex=gex)
+        assert plan.S >= 2
+        out = oz2.oz2_gemm(A, B, 212, g_ex=gex)
+        err[gex] = abs(expansion_value(out[0, 0]) - ex)
+    assert err[k] <= ulp_p(ex, 212)                     # the guarded plan meets Prop. 2
+    assert err[0] > ulp_p(ex, 212)                      # without it the truncation shows
