@@ -216,7 +216,8 @@ int ozlu_get_stats(ozlu_handle* handle, ozlu_stats* out);
  * handle and allocates neither device nor host memory.
  *   Arguments as ozlu_gemm (without handle and options), plus the stream
  *   (cudaStream_t as void*, NULL = default stream); A, B, C must be device
- *   pointers (a host pointer is rejected as an invalid argument), k >= 1.
+ *   pointers of the current device (a host pointer, or one into another
+ *   GPU's memory, is rejected as an invalid argument), k >= 1.
  *   Scratch: one fixed 16 MiB device array inside the library, held by every
  *   GPU that loads it until the process exits.  Problems whose intermediates
  *   do not fit (for QD, m = n = k = 256 fits; 384 does not) return
@@ -226,7 +227,11 @@ int ozlu_get_stats(ozlu_handle* handle, ozlu_stats* out);
  *   first call before any stream capture.
  *   All calls share the array: calls that overlap on the GPU (other streams,
  *   other host threads) race and must be serialised by the caller.  Nothing
- *   needs clearing between calls: every byte read is written first.
+ *   needs clearing between calls: each call writes the exponents, the residue
+ *   rows of A and B with their zero K padding, and the t values before it
+ *   reads them; the padding rows of the residue planes (beyond m and n, up to
+ *   the next multiple of 128) may keep bytes of an earlier call, and those
+ *   only reach output tiles outside m x n, which are discarded.
  * Returns 0, -i for invalid argument i (nc = 1), or an OZLU_ERR_* code; the
  * work is stream ordered (the call does not wait for it).
  */
@@ -295,6 +300,33 @@ int ozlu_mp_plan(int p, int k, ozlu_plan_info* out);
 /* Solve A X = B from ozlu_mp_getrf's factors; B is n x nrhs (p-bit), overwritten. */
 int ozlu_mp_getrs(ozlu_handle* handle, int p, int n, int nrhs, const ozlu_mp_matrix* LU, const int* ipiv,
                   const ozlu_mp_matrix* B);
+
+/*
+ * Test hooks for failure handling (no counterpart in the paper).  Neither
+ * faults the GPU: the failures are made on the host or by a wait that runs
+ * out on a flag nothing sets.
+ *
+ * ozlu_debug_fail_alloc: the next `count` device allocations the library
+ * makes (handle workspaces and scratch) fail as if cudaMalloc had failed, so
+ * the calls that needed them return OZLU_ERR_NOMEM; 0 turns it off.  The
+ * counter is process-wide.  Returns 0, or -1 for count < 0.
+ *
+ * ozlu_debug_wait_expiry: runs one of the library's bounded device waits on
+ * the handle's stream with a short limit, on a flag or barrier that nothing
+ * sets, and then the LU's finish step that turns the error word into info:
+ *   which 1  the panel kernel's stamp wait (limit in ns of the global timer);
+ *            its error word is the panel scratch of the handle
+ *   which 2  the tensor-core GEMM's mbarrier wait (limit in polls of ~0.1 us);
+ *            its error word is the handle's (ozlu_debug_fetch what = 6)
+ * out (host, 3 ints): 1 if the wait gave up, the error word after it
+ * (OZLU_ERR_TIMEOUT), and the info the finish step wrote (-OZLU_ERR_TIMEOUT).
+ * Waits for the stream.  Returns OZLU_ERR_TIMEOUT when the wait gave up (as
+ * ozlu_getrf does with host arguments), 0 if it did not, -i for an invalid
+ * argument i, or OZLU_ERR_CUDA / OZLU_ERR_NOMEM.  The next ozlu_gemm,
+ * ozlu_getrf or ozlu_getrs call clears both error words.
+ */
+int ozlu_debug_fail_alloc(int count);
+int ozlu_debug_wait_expiry(ozlu_handle* handle, int which, long long limit, int* out);
 
 /* Version string of the library. */
 const char* ozlu_version(void);

@@ -1,7 +1,9 @@
 // C ABI entry points, handle and device workspace.
 #include <string.h>
 
+#include <atomic>
 #include <map>
+#include <mutex>
 #include <tuple>
 
 #include "ozlu_internal.h"
@@ -10,6 +12,53 @@
 namespace ozlu {
 
 int cuda_rc(cudaError_t e) { return e == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA; }
+
+namespace {
+std::atomic<int> g_fail_allocs{0};  // allocations still to fail (test injection)
+std::mutex g_attr_mutex;
+std::map<std::pair<const void*, int>, int> g_smem_set;  // (kernel, device) -> bytes set
+constexpr int MAX_DEVICES = 64;
+std::atomic<int> g_sms[MAX_DEVICES];
+}  // namespace
+
+bool dev_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    for (int v = g_fail_allocs.load(); v > 0; v = g_fail_allocs.load())
+        if (g_fail_allocs.compare_exchange_weak(v, v - 1)) return false;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return false;
+    }
+    return true;
+}
+
+void raise_smem_limit(const void* kernel, int bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return;
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    auto key = std::make_pair(kernel, dev);
+    auto it = g_smem_set.find(key);
+    if (it != g_smem_set.end() && it->second >= bytes) return;
+    if (cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes) == cudaSuccess)
+        g_smem_set[key] = bytes;
+    else
+        cudaGetLastError();
+}
+
+int device_sms() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+    if (dev < MAX_DEVICES) {
+        const int v = g_sms[dev].load();
+        if (v > 0) return v;
+    }
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms < 1) sms = 1;
+    if (dev < MAX_DEVICES) g_sms[dev].store(sms);
+    return sms;
+}
 
 bool is_device_ptr(const void* p) {
     if (!p) return false;
@@ -25,8 +74,7 @@ bool is_device_ptr(const void* p) {
 // tensor-core GEMM); allocated once, zeroed in stream order by each call
 int* err_word(ozlu_handle* h) {
     if (!h->dev_err) {
-        if (cudaMalloc(&h->dev_err, 256) != cudaSuccess) {
-            cudaGetLastError();
+        if (!dev_alloc((void**)&h->dev_err, 256)) {
             h->dev_err = nullptr;
             return nullptr;
         }
@@ -47,10 +95,8 @@ int Workspace::ensure(size_t bytes) {
     base = nullptr;
     cap = 0;
     size_t want = bytes + bytes / 8;
-    if (cudaMalloc(&base, want) != cudaSuccess) {
-        cudaGetLastError();
-        if (cudaMalloc(&base, bytes) != cudaSuccess) {
-            cudaGetLastError();
+    if (!dev_alloc(&base, want)) {
+        if (!dev_alloc(&base, bytes)) {
             base = nullptr;
             return OZLU_ERR_NOMEM;
         }
@@ -291,7 +337,13 @@ using namespace ozlu;
 
 extern "C" {
 
-const char* ozlu_version(void) { return "ozlu 0.1 (sm_103a)"; }
+const char* ozlu_version(void) { return "ozlu 0.2 (sm_103a)"; }
+
+int ozlu_debug_fail_alloc(int count) {
+    if (count < 0) return -1;
+    g_fail_allocs.store(count);
+    return OZLU_OK;
+}
 
 int ozlu_create(ozlu_handle** handle, void* stream) {
     if (!handle) return -1;

@@ -181,11 +181,7 @@ __global__ void __launch_bounds__(THREADS) gemm_imma_kernel(
 void launch_gemm_imma(const int8_t* RA, const int8_t* RB, int m, int n, int Mpad, int Npad,
                       int Kpad, const DevTable& tab, uint8_t* T, cudaStream_t s) {
     const int smem = STAGES * 2 * TILE_BYTES;  // 64 KB
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(gemm_imma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        attr_set = true;
-    }
+    raise_smem_limit((const void*)gemm_imma_kernel, smem);
     dim3 grid(Mpad / BM, Npad / BN, tab.N * tab.G);
     gemm_imma_kernel<<<grid, THREADS, smem, s>>>(RA, RB, m, n, Mpad, Npad, Kpad, tab, T);
 }

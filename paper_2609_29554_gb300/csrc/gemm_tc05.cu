@@ -61,12 +61,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* b, uint32_t parity) {
     return ok != 0;
 }
 
-// bounded wait: false (and the error word set) after WAIT_LIMIT tries
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err, volatile int* abort) {
+// bounded wait: false (and the error word set) after `limit` tries
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err, volatile int* abort,
+                                          long long limit = WAIT_LIMIT) {
     long long it = 0;
     while (!mbar_try_wait(b, parity)) {
         if (*abort) return false;
-        if (++it > WAIT_LIMIT) {
+        if (++it > limit) {
             atomicExch(err, OZLU_ERR_TIMEOUT);
             *abort = 1;
             return false;
@@ -318,6 +319,21 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc05_kernel(
     }
 }
 
+// Self-test of the bounded mbarrier wait: one thread waits with the kernel's
+// own wait routine on a barrier nothing ever arrives at (phase 0 of a fresh
+// barrier), with a short iteration limit; out[0] = 1 if the wait gave up.
+// No TMA, MMA or TMEM is involved.
+__global__ void mbar_expiry_selftest_kernel(long long limit, int* err, int* out) {
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ int abort_flag;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    const bool ok = mbar_wait(&bar, 0, err, &abort_flag, limit);
+    out[0] = ok ? 0 : 1;
+}
+
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
@@ -347,6 +363,11 @@ bool make_map(CUtensorMap* tm, const void* base, bool fp8, int Kpad, long long r
 
 }  // namespace
 
+int launch_mbar_expiry_selftest(long long limit, int* err, int* out, cudaStream_t s) {
+    mbar_expiry_selftest_kernel<<<1, 32, 0, s>>>(limit, err, out);
+    return cudaGetLastError() == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
+}
+
 size_t tc05_smem_bytes() { return 2 * STAGES * TILE + 2 * STAGES * 8 + 4 * 8 + 16 + 1024; }
 
 int launch_gemm_tc05(bool fp8, const void* RA, const void* RB, int m, int n, int Mpad, int Npad, int Kpad,
@@ -357,27 +378,14 @@ int launch_gemm_tc05(bool fp8, const void* RA, const void* RB, int m, int n, int
     if (!make_map(&tb, RB, fp8, Kpad, (long long)tab.N * tab.S * P * Npad)) return OZLU_ERR_UNSUPPORTED;
     const int KB = Kpad * (fp8 ? 1 : 2) / BK;
     const size_t smem = tc05_smem_bytes();
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    }
+    const int sms = device_sms();
     const long long tiles = (long long)(Mpad / BM) * (Npad / BN) * tab.N * tab.G;
     dim3 grid((unsigned)(tiles < sms ? tiles : sms));
     if (fp8) {
-        static bool set = false;
-        if (!set) {
-            cudaFuncSetAttribute(gemm_tc05_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            set = true;
-        }
+        raise_smem_limit((const void*)gemm_tc05_kernel<true>, (int)smem);
         gemm_tc05_kernel<true><<<grid, THREADS, smem, s>>>(ta, tb, m, n, Mpad, Npad, KB, tab, T, err);
     } else {
-        static bool set = false;
-        if (!set) {
-            cudaFuncSetAttribute(gemm_tc05_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            set = true;
-        }
+        raise_smem_limit((const void*)gemm_tc05_kernel<false>, (int)smem);
         gemm_tc05_kernel<false><<<grid, THREADS, smem, s>>>(ta, tb, m, n, Mpad, Npad, KB, tab, T, err);
     }
     return cudaGetLastError() == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;

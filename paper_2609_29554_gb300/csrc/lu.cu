@@ -382,16 +382,18 @@ __device__ __forceinline__ unsigned long long ld_volatile(const unsigned long lo
 }
 
 // wait until the stamp word carries column `want`; returns it, or 0 on
-// expiry (the error word is then set) or when another block has given up
+// expiry after limit_ns of the global timer (the error word is then set) or
+// when another block has given up
 __device__ __forceinline__ unsigned long long wait_stamp(const unsigned long long* p, unsigned want,
-                                                         int* err) {
+                                                         int* err,
+                                                         unsigned long long limit_ns = COOP_WAIT_NS) {
     const unsigned long long t0 = global_ns();
     for (int it = 1;; ++it) {
         const unsigned long long v = ld_volatile(p);
         if ((unsigned)(v >> STAMP_SHIFT) == want) return v;
         if ((it & 63) == 0) {
             if (*(volatile int*)err) return 0;
-            if (global_ns() - t0 > COOP_WAIT_NS) {
+            if (global_ns() - t0 > limit_ns) {
                 atomicExch(err, OZLU_ERR_TIMEOUT);
                 return 0;
             }
@@ -779,12 +781,7 @@ void laswp2(double* A, long long lda, int ja0, int ja1, int jb0, int jb1, int k0
     }
     laswp_list_kernel<<<1, 256, 0, s>>>(k0, k1, ipiv, list);
     const size_t smem = sizeof(double) * 2 * (k1 - k0) * LCT * N;
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(laswp_apply_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(double) * 2 * LMAXB * LCT * N));
-        attr = true;
-    }
+    raise_smem_limit((const void*)laswp_apply_kernel<N>, (int)(sizeof(double) * 2 * LMAXB * LCT * N));
     if (ja1 > ja0) laswp_apply_kernel<N><<<(ja1 - ja0 + LCT - 1) / LCT, 256, smem, s>>>(A, lda, ja0, ja1, list);
     if (jb1 > jb0) laswp_apply_kernel<N><<<(jb1 - jb0 + LCT - 1) / LCT, 256, smem, s>>>(A, lda, jb0, jb1, list);
 }
@@ -891,11 +888,7 @@ void trsm_base(const double* T, long long ldt, double* X, long long ldx, int b, 
     // 8 columns (warps) per block, fewer when that leaves SMs idle
     const int wpb = ncols >= 8 * 152 ? 8 : (ncols >= 4 * 152 ? 4 : 2);
     const size_t smem = sizeof(MPF<L>) * (BASE * BASE + BASE);
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(trsm_base_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    raise_smem_limit((const void*)trsm_base_kernel<N>, (int)smem);
     trsm_base_kernel<N><<<(ncols + wpb - 1) / wpb, 32 * wpb, smem, s>>>(sc, X, ldx, b, ncols, lower);
 }
 
@@ -905,9 +898,7 @@ template <int N>
 bool base_block_coop(double* A, long long lda, int n, int c0, int b, int p0, int p1, int* ipiv,
                      int* info, void* scratch, int min_rows, cudaStream_t s) {
     constexpr int L = Limbs<N>::L;
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = device_sms();
     // at least min_rows rows per block: a small panel takes a few SMs and
     // leaves the rest to concurrent work (the batched driver runs instances
     // side by side and asks for 32, single factorisations for 16)
@@ -919,8 +910,7 @@ bool base_block_coop(double* A, long long lda, int n, int c0, int b, int p0, int
         const int rows = (n - c0 + G - 1) / G;
         const size_t smem = sizeof(MPF<L>) * (size_t)rows * (b + 1);
         if (smem > 200 * 1024 / per_sm) continue;
-        cudaFuncSetAttribute(base_block_coop_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(smem < 1024 ? 1024 : smem));
+        raise_smem_limit((const void*)base_block_coop_kernel<N>, (int)(smem < 1024 ? 1024 : smem));
         int active = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&active, base_block_coop_kernel<N>, COOP_THREADS,
                                                       smem);
@@ -1119,7 +1109,57 @@ __global__ void finish_kernel(int* info_out, const LuScratch* sc, const int* coo
     else if (*gerr) v = -*gerr;
     *info_out = v;
 }
+
+// Self-test of the panel kernel's bounded wait: one thread waits with
+// wait_stamp for a stamp that nothing writes (a zeroed word, column 1), with a
+// short limit, into the panel's own error word; out[0] = 1 if it gave up.
+__global__ void stamp_expiry_selftest_kernel(const unsigned long long* word, unsigned long long limit_ns,
+                                             int* err, int* out) {
+    if (threadIdx.x != 0) return;
+    out[0] = wait_stamp(word, 1u, err, limit_ns) == 0 ? 1 : 0;
+}
 }  // namespace
+
+int launch_mbar_expiry_selftest(long long limit, int* err, int* out, cudaStream_t s);
+
+// which = 1: the panel's stamp wait, then the factorisation's finish step
+// (info); which = 2: the tensor-core GEMM's mbarrier wait.  out (host, 3
+// ints): whether the wait gave up, the error word, info (which = 1).
+int wait_expiry_selftest(ozlu_handle* h, int which, long long limit, int* out) {
+    LuScratch* sc;
+    int rc = lu_scratch(h, &sc);
+    if (rc) return rc;
+    cudaStream_t s = h->stream;
+    int* gerr = err_word(h);
+    if (!gerr) return OZLU_ERR_NOMEM;
+    if (cudaMemsetAsync(sc, 0, sizeof(LuScratch), s)) return OZLU_ERR_CUDA;
+    if ((rc = coop_reset(h, 4, s))) return rc;
+    if ((rc = clear_err_word(h))) return rc;
+    // the candidate area of the scratch (zeroed above) holds a stamp word that
+    // nothing writes and the kernel's flag
+    unsigned long long* word = reinterpret_cast<unsigned long long*>(&sc->pval[0][0]);
+    int* flag = &sc->pidx[0];
+    if (which == 1) {
+        stamp_expiry_selftest_kernel<<<1, 32, 0, s>>>(word, (unsigned long long)limit,
+                                                       (int*)h->coop_scratch, flag);
+        finish_kernel<<<1, 1, 0, s>>>(&sc->result, sc, (const int*)h->coop_scratch, gerr);
+    } else if (which == 2) {
+        if ((rc = launch_mbar_expiry_selftest(limit, gerr, flag, s))) return rc;
+        finish_kernel<<<1, 1, 0, s>>>(&sc->result, sc, (const int*)h->coop_scratch, gerr);
+    } else {
+        return -2;
+    }
+    if (cudaGetLastError() != cudaSuccess) return OZLU_ERR_CUDA;
+    int host[3] = {0, 0, 0};
+    if (cudaMemcpyAsync(&host[0], flag, sizeof(int), cudaMemcpyDeviceToHost, s) ||
+        cudaMemcpyAsync(&host[1], which == 1 ? (const int*)h->coop_scratch : gerr, sizeof(int),
+                        cudaMemcpyDeviceToHost, s) ||
+        cudaMemcpyAsync(&host[2], &sc->result, sizeof(int), cudaMemcpyDeviceToHost, s) ||
+        cudaStreamSynchronize(s))
+        return OZLU_ERR_CUDA;
+    for (int i = 0; i < 3; ++i) out[i] = host[i];
+    return host[2] < 0 ? -host[2] : OZLU_OK;
+}
 
 // one factorisation on device pointers (the batched driver calls it per
 // instance on its own streams); info of the instance goes to *info_out
@@ -1160,15 +1200,11 @@ int getrs_one(ozlu_handle* h, int nc, int p, int n, int nrhs, const double* LU, 
 
 int lu_scratch(ozlu_handle* h, LuScratch** out) {
     if (!h->lu_scratch) {
-        if (cudaMalloc(&h->lu_scratch, sizeof(LuScratch)) != cudaSuccess) {
-            cudaGetLastError();
-            return OZLU_ERR_NOMEM;
-        }
+        if (!dev_alloc(&h->lu_scratch, sizeof(LuScratch))) return OZLU_ERR_NOMEM;
     }
     if (!h->coop_scratch) {
         h->coop_bytes = sizeof(CoopScratch<8>);
-        if (cudaMalloc(&h->coop_scratch, h->coop_bytes) != cudaSuccess) {
-            cudaGetLastError();
+        if (!dev_alloc(&h->coop_scratch, h->coop_bytes)) {
             h->coop_scratch = nullptr;
             return OZLU_ERR_NOMEM;
         }
@@ -1245,6 +1281,15 @@ extern "C" int ozlu_getrf(ozlu_handle* h, int nc, int p, int n, double* A, long 
         return OZLU_ERR_CUDA;
     if (!dA || !dP || !dI) return cuda_rc(cudaStreamSynchronize(s));
     return OZLU_OK;
+}
+
+extern "C" int ozlu_debug_wait_expiry(ozlu_handle* h, int which, long long limit, int* out) {
+    if (!h) return -1;
+    if (which != 1 && which != 2) return -2;
+    if (limit < 1) return -3;
+    if (!out) return -4;
+    if (cudaSetDevice(h->device) != cudaSuccess) return OZLU_ERR_CUDA;
+    return wait_expiry_selftest(h, which, limit, out);
 }
 
 extern "C" int ozlu_getrs(ozlu_handle* h, int nc, int p, int n, int nrhs, const double* LU,

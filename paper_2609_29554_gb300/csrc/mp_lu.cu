@@ -262,8 +262,7 @@ struct Scratch {
     int alloc(int L, long long cnt) {
         const int L1 = L + 1;
         const size_t words = 4 * ((size_t)L1 + 2) + ((size_t)L + 2) * (size_t)cnt + 16;
-        if (cudaMalloc(&mem, words * 4) != cudaSuccess) {
-            cudaGetLastError();
+        if (!dev_alloc(&mem, words * 4)) {
             mem = nullptr;
             return OZLU_ERR_NOMEM;
         }

@@ -12,15 +12,21 @@
 // The first call on a device looks up the device address of the array with
 // cudaGetSymbolAddress, with that device current, and caches it; that first
 // call should come before any stream capture.  Every call reuses the same
-// array and leaves its contents behind; the kernels overwrite every byte they
-// later read (padding included), so nothing needs clearing between calls.
-// Calls that overlap on the GPU (on different streams, or from different
-// host threads) race on the array: serialise them.
+// array and leaves its contents behind.  Each call writes the parts of the
+// array its results depend on before reading them: shared exponents, the
+// residue rows of A and B with their zero K padding, and the t values.  The
+// padding rows of the residue planes (row m to the next multiple of 128, and
+// likewise for n) are not written and may hold bytes of an earlier call; the
+// GEMM reads them, but they only reach output tiles outside m x n, which are
+// discarded.  So nothing needs clearing between calls.  Calls that overlap
+// on the GPU (on different streams, or from different host threads) race on
+// the array: serialise them.
 //
 // Back-end: INT8 residues on mma.sync (the same kernels as ozlu_gemm's INT8
 // path), so results equal ozlu_gemm with backend OZLU_BE_INT8 bit for bit.
-// The plan follows the same rule as the handle's planner, recomputed here
-// with fixed-size arrays so that no host memory is allocated either.
+// The plan follows the same rule as the handle's planner, recomputed with
+// fixed-size arrays so that no host memory is allocated either
+// (plan_noalloc, noalloc_plan.cpp).
 #include <math.h>
 #include <string.h>
 
@@ -35,7 +41,6 @@ constexpr size_t NOALLOC_SCRATCH_BYTES = 16u << 20;  // 16 MiB
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
 constexpr int MAXDEV = 64;
-constexpr int PW = 16;  // words of P (54 moduli of <= 8 bits: <= 432 bits)
 
 std::mutex g_mutex;
 void* g_scratch_ptr[MAXDEV] = {nullptr};
@@ -57,114 +62,21 @@ int scratch_ptr(void** out) {
     return OZLU_OK;
 }
 
-bool is_prime_na(int v) {
-    if (v < 2) return false;
-    for (int d = 2; d * d <= v; ++d)
-        if (v % d == 0) return false;
-    return true;
-}
-
-// the 54 maximal prime powers <= 255, descending (Sec. 3.2)
-int int8_moduli_na(int* out) {
-    int cnt = 0;
-    for (int q = 2; q <= 255; ++q) {
-        if (!is_prime_na(q)) continue;
-        int v = q;
-        while (v * q <= 255) v *= q;
-        out[cnt++] = v;
-    }
-    for (int i = 0; i < cnt; ++i)
-        for (int j = i + 1; j < cnt; ++j)
-            if (out[j] > out[i]) { const int t = out[i]; out[i] = out[j]; out[j] = t; }
-    return cnt;
-}
-
-int inv_mod_na(int a, int m) {
-    long long t = 0, nt = 1, r = m, nr = a % m;
-    while (nr) {
-        const long long q = r / nr;
-        long long tmp = t - q * nt; t = nt; nt = tmp;
-        tmp = r - q * nr; r = nr; nr = tmp;
-    }
-    return (int)(t < 0 ? t + m : t);
-}
-
-// INT8 plan of Sec. 3.2 into a DevTable, fixed-size arrays only
-int plan_na(int p, int K, DevTable& t, int& Kpad_out) {
-    memset(&t, 0, sizeof t);
-    if (p < 1 || K < 1) return OZLU_ERR_CAPACITY;
-    int mods[64];
-    const int nm = int8_moduli_na(mods);
-    const int slack = (int)ceil(log2(2.0 * K) - 1e-12) + 16;
-    const int Kpad = (K + 127) / 128 * 128;
-    for (int S = 1; S <= 64; ++S) {
-        if ((double)Kpad * S * 127.0 * 127.0 >= ldexp(1.0, 31)) continue;
-        const int w = (p + slack + S - 1) / S;
-        const double need = 2.0 * w + log2((double)K) + log2((double)S) + 5.0;
-        double cum = 0.0;
-        int N = 0;
-        for (int i = 0; i < nm; ++i) {
-            cum += log2((double)mods[i]);
-            if (cum > need) { N = i + 1; break; }
-        }
-        if (N == 0) continue;
-        const int g0 = S - 1, G = S;
-        const int sbar_bits = 2 * w - 1 + (int)ceil(log2((double)S * K) - 1e-12) + 1;
-        const int WG = (sbar_bits + 31) / 32;
-        const int pint_bits = w * (2 * S - 2 - g0) + sbar_bits;
-        const int WX = (w * S + 1 + 31) / 32;
-        const int H = (w + 1 + 15) / 16;
-        if (WG > MAXWG || WX > MAXWX || H > MAXH || G > MAXG || pint_bits + 2 > WINDOW_BITS)
-            return OZLU_ERR_CAPACITY;
-        // P and M_l as little-endian 32-bit words
-        uint32_t P[PW] = {1};
-        for (int i = 0; i < N; ++i) {
-            uint64_t c = 0;
-            for (int wd = 0; wd < PW; ++wd) {
-                const uint64_t v = (uint64_t)P[wd] * (uint32_t)mods[i] + c;
-                P[wd] = (uint32_t)v;
-                c = v >> 32;
-            }
-        }
-        t.N = N; t.WG = WG; t.H = H; t.S = S; t.w = w; t.g0 = g0; t.G = G; t.Q = w * S; t.WX = WX;
-        for (int l = 0; l < N; ++l) {
-            const uint32_t m = (uint32_t)mods[l];
-            uint32_t M[PW];
-            uint64_t rem = 0;
-            for (int wd = PW - 1; wd >= 0; --wd) {
-                const uint64_t cur = (rem << 32) | P[wd];
-                M[wd] = (uint32_t)(cur / m);
-                rem = cur % m;
-            }
-            uint64_t mm = 0;
-            for (int wd = PW - 1; wd >= 0; --wd) mm = ((mm << 32) | M[wd]) % m;
-            t.mod[l] = (int)m;
-            t.y[l] = inv_mod_na((int)mm, (int)m);
-            t.magic[l] = (uint32_t)(((1ull << 32) + m - 1) / m);
-            t.invm[l] = 1.0f / (float)m;
-            uint64_t r = 1 % m;
-            for (int j = 0; j < MAXH; ++j) {
-                t.pow16[l][j] = (uint32_t)r;
-                r = (r << 16) % m;
-            }
-            for (int wd = 0; wd < MAXWG; ++wd) t.Mlow[l][wd] = wd < PW ? M[wd] : 0u;
-        }
-        for (int wd = 0; wd < MAXWG; ++wd) t.Plow[wd] = wd < PW ? P[wd] : 0u;
-        Kpad_out = Kpad;
-        return OZLU_OK;
-    }
-    return OZLU_ERR_CAPACITY;
-}
-
 size_t up256(size_t v) { return (v + 255) / 256 * 256; }
 
+// device (or managed) memory of the current device: a pointer into another
+// GPU's memory is rejected like a host pointer
 bool on_device(const void* p) {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    if (a.type != cudaMemoryTypeDevice) return false;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    return a.device == dev;
 }
 
 }  // namespace
@@ -192,7 +104,7 @@ extern "C" int ozlu_gemm_noalloc(int nc, int p, int m, int n, int k, int alpha, 
     if (m == 0 || n == 0) return OZLU_OK;
     DevTable tab;
     int Kpad = 0;
-    int rc = plan_na(p, k, tab, Kpad);
+    int rc = plan_noalloc(p, k, tab, Kpad);
     if (rc) return rc;
     const int Mpad = (m + 127) / 128 * 128, Npad = (n + 127) / 128 * 128;
     size_t off = 0;

@@ -43,9 +43,21 @@ struct DevTable {
     uint32_t Plow[MAXWG];          // P mod 2^(32 WG)
 };
 
+// device memory of the library: cudaMalloc unless a test has asked for the
+// next allocations to fail (ozlu_debug_fail_alloc); returns false on failure
+bool dev_alloc(void** p, size_t bytes);
+// raise a kernel's dynamic shared-memory limit on the current device (the
+// attribute is per device; each (kernel, device) pair is set once)
+void raise_smem_limit(const void* kernel, int bytes);
+// SM count of the current device (cached per device)
+int device_sms();
+
 int make_plan(int p, int K, const ozlu_opts* o, Plan& out);
 int make_plan_mp(int p, int K, Plan& out);  // p-bit multi-limb inputs, INT8
 void fill_table(const Plan& pl, DevTable& t);
+// the allocation-free GEMM's planner: the INT8 plan straight into a table,
+// fixed-size arrays only (no host allocation)
+int plan_noalloc(int p, int K, DevTable& t, int& Kpad);
 
 // ---------------------------------------------------------------- kernels --
 // (S1) shared exponents: mu[i] over rows of A (m x k), nu[j] over columns of B.

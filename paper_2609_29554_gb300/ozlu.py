@@ -85,6 +85,8 @@ SIGNATURES = {
     "ozlu_mp_getrf": (_I, [_P, _I, _I, ctypes.POINTER(ozlu_mp_matrix), _P, _I, _P]),
     "ozlu_mp_getrs": (_I, [_P, _I, _I, _I, ctypes.POINTER(ozlu_mp_matrix), _P,
                            ctypes.POINTER(ozlu_mp_matrix)]),
+    "ozlu_debug_fail_alloc": (_I, [_I]),
+    "ozlu_debug_wait_expiry": (_I, [_P, _I, _L, _P]),
 }
 
 
@@ -222,6 +224,17 @@ def ozlu_getrs_batched(h, nc, p, ns, nrhs, lus, lds, pivs, bs, ldbs, opts=None):
 def ozlu_debug_fetch(h, what, out: np.ndarray):
     _check("ozlu_debug_fetch", lib().ozlu_debug_fetch(h, what, out.ctypes.data, out.nbytes))
     return out
+
+
+def ozlu_debug_fail_alloc(count):
+    _check("ozlu_debug_fail_alloc", lib().ozlu_debug_fail_alloc(int(count)))
+
+
+def ozlu_debug_wait_expiry(h, which, limit):
+    """Return code and (gave_up, error_word, info) of one bounded-wait self-test."""
+    out = np.zeros(3, dtype=np.int32)
+    rc = lib().ozlu_debug_wait_expiry(h, which, int(limit), out.ctypes.data)
+    return rc, tuple(int(v) for v in out)
 
 
 def ozlu_set_timing(h, enable):

@@ -2,6 +2,8 @@
 // builds the plan and the DevTable every kernel reads for a few precisions and
 // prints them for an exact comparison with the oracle's integers in Python.
 //
+// Backend code 0 is the p-bit planner, -1 the allocation-free GEMM's planner
+// (plan_noalloc, which writes the table directly).
 // Output per plan: "plan p K backend S w N WG", then per modulus
 // "mod l m y magic invm(hex float) pow16[0..MAXH) Mlow[0..MAXWG)", then
 // "Plow Plow[0..MAXWG)".
@@ -15,8 +17,12 @@ int main(int argc, char** argv) {
     for (int i = 1; i + 2 < argc; i += 3) {
         const int p = atoi(argv[i]), K = atoi(argv[i + 1]), be = atoi(argv[i + 2]);
         Plan pl;
+        DevTable t;
         int rc;
-        if (be == 0) {
+        if (be == -1) {
+            int kpad = 0;
+            rc = plan_noalloc(p, K, t, kpad);
+        } else if (be == 0) {
             rc = make_plan_mp(p, K, pl);
         } else {
             ozlu_opts o = {};
@@ -27,8 +33,7 @@ int main(int argc, char** argv) {
             printf("fail %d %d %d %d\n", p, K, be, rc);
             continue;
         }
-        DevTable t;
-        fill_table(pl, t);
+        if (be != -1) fill_table(pl, t);
         printf("plan %d %d %d %d %d %d %d\n", p, K, be, t.S, t.w, t.N, t.WG);
         for (int l = 0; l < t.N; ++l) {
             printf("mod %d %d %d %u %a", l, t.mod[l], t.y[l], t.magic[l], (double)t.invm[l]);

@@ -62,3 +62,21 @@ def test_tc05_full_size_sampled(be, n):
     cols = np.sort(rng.choice(n, 4, replace=False))
     ref = oz2.oz2_gemm(A[rows], B[:, cols], 212, backend=be)
     np.testing.assert_array_equal(out[np.ix_(rows, cols)], ref)
+
+
+@pytest.mark.parametrize("be", ["fp16", "int8"])
+def test_lu_update_shape_full_size_sampled(be):
+    # the trailing update of the benchmark's first LU step: m = n = 3840,
+    # K = nb = 256, C <- C - A B (Eq. (13)); sampled outputs against the oracle
+    m, k = 3840, 256
+    A, B = _pair(m, k, m, 4, 3840, -3, 3)
+    C = random_expansions(m, m, 4, 3841, -2, 4)
+    out = gpu_gemm(A, B, alpha=-1, beta=1, C=C, opts=ozlu.make_opts(be))
+    h = handle()
+    assert ozlu.ozlu_debug_fetch(h, 6, np.zeros(1, np.int32))[0] == 0
+    rng = np.random.default_rng(7)
+    rows = np.sort(np.concatenate([rng.choice(m, 5, replace=False), [0, m - 1]]))
+    cols = np.sort(np.concatenate([rng.choice(m, 5, replace=False), [0, m - 1]]))
+    ref = oz2.oz2_gemm(A[rows], B[:, cols], 212, alpha=-1, beta=1, C=C[np.ix_(rows, cols)],
+                       backend=be)
+    np.testing.assert_array_equal(out[np.ix_(rows, cols)], ref)

@@ -18,13 +18,16 @@ from oracle.plan import make_plan
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = [os.path.join(ROOT, "tests", "plan_host", "plan_host.cpp"),
-       os.path.join(ROOT, "paper_2609_29554_gb300", "csrc", "plan.cpp")]
+       os.path.join(ROOT, "paper_2609_29554_gb300", "csrc", "plan.cpp"),
+       os.path.join(ROOT, "paper_2609_29554_gb300", "csrc", "noalloc_plan.cpp")]
 INC = os.path.join(ROOT, "paper_2609_29554_gb300", "csrc")
 MAXH, MAXWG = 16, 16
-BACKENDS = {0: "int8", 1: "int8", 2: "fp8", 3: "fp64", 4: "fp16"}   # 0: the p-bit planner
+# 0: the p-bit planner; -1: the allocation-free GEMM's planner (INT8)
+BACKENDS = {-1: "int8", 0: "int8", 1: "int8", 2: "fp8", 3: "fp64", 4: "fp16"}
 CONFIGS = [(106, 32, 1), (159, 512, 1), (212, 256, 1), (212, 4096, 1), (212, 256, 2),
            (212, 256, 4), (106, 512, 3), (212, 512, 3), (3136, 256, 0), (12544, 256, 0),
-           (64, 1, 0)]
+           (64, 1, 0), (106, 19, -1), (159, 256, -1), (212, 256, -1), (212, 100, -1),
+           (150, 4096, -1)]
 
 
 def _cuda_include():
@@ -83,3 +86,13 @@ def test_table_matches_oracle(tables, cfg):
         assert magic == -(-(1 << 32) // m)
         assert invm == float(np.float32(1.0) / np.float32(m))
     assert tab["Plow"] == _words(ref.P & mask, MAXWG)
+
+
+@pytest.mark.parametrize("p,K", [(106, 19), (159, 256), (212, 256), (212, 100), (150, 4096)])
+def test_noalloc_table_equals_handle_planner(tables, p, K):
+    # the allocation-free GEMM keeps its own fixed-array planner: its table
+    # must be the handle planner's INT8 table entry for entry
+    na = tables[(p, K, -1)]
+    assert na["N"] > 0
+    ref = make_plan(p, K, backend="int8")
+    assert (na["S"], na["w"], na["N"]) == (ref.S, ref.w, ref.N)

@@ -49,10 +49,14 @@ def _noalloc(oz, A, B, C, alpha, beta):
 
 
 def test_noalloc_matches_gemm_on_consecutive_calls(oz):
+    # consecutive calls share the library's array: each case runs twice in a
+    # row, the cases differ in size and data, and the first case is repeated
+    # at the end, after the array has held other problems' intermediates
     h = oz.ozlu_create(None)
     try:
         cases = [((100, 120, 90, 4), -1, 1, 11), ((256, 256, 256, 4), 1, 0, 12),
-                 ((37, 19, 29, 2), 1, 1, 13)]
+                 ((37, 19, 29, 2), 1, 1, 13), ((64, 300, 50, 3), -1, 1, 14),
+                 ((100, 120, 90, 4), -1, 1, 11)]
         for (m, k, n, nc), alpha, beta, seed in cases:
             A = random_expansions(m, k, nc, seed, -20, 20)
             B = random_expansions(k, n, nc, seed + 100, -20, 20)
