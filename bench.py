@@ -624,11 +624,13 @@ def accuracy(ozlu, h, A0, LU, ipiv, n, nc, opts):
 
 
 def compare(ozlu, h, A0, A, ipiv, info, n, nb, nc, a):
-    """Single-instance INT8 Ozaki-II LU and the native blocked-naive LU (same matrix)."""
+    """Single-instance INT8 Ozaki-II LU and the native blocked-naive and
+    unblocked-naive expansion LUs (Sec. 3.4), on the same matrix."""
     import torch
     out = {}
     for name, opts in (("ozaki2_int8_single_instance", ozlu.make_opts("int8", graph=1)),
-                       ("native_blocked_expansion_lu", ozlu.make_opts("int8", native=1, graph=1))):
+                       ("native_blocked_expansion_lu", ozlu.make_opts("int8", native=1, graph=1)),
+                       ("native_unblocked_expansion_lu", ozlu.make_opts("int8", native=2, graph=1))):
         for _ in range(2):                           # eager, then capture
             A.copy_(A0)
             ozlu.ozlu_getrf(h, nc, 0, n, A, n, ipiv, nb, info, opts)

@@ -70,7 +70,10 @@ typedef struct {
     int g_ex;         /* extra guard bits in the slack of Sec. 3.2                 */
     int native;       /* ozlu_getrf only: 1 = trailing update (P4) by per-element
                          multiply-adds in expansion arithmetic, the "blocked naive"
-                         comparison of Sec. 3.4 (panels unchanged)                */
+                         comparison of Sec. 3.4 (panels unchanged); 2 = the
+                         "unblocked naive" LU of Sec. 3.4 (b = 1: pivot, scale
+                         and a rank-1 update of the whole trailing matrix in
+                         expansion arithmetic for every column; nb is ignored) */
     int graph;        /* ozlu_getrf/ozlu_getrs (device pointers) and the batched
                          calls: 1 = capture the call's work in a CUDA graph on the
                          second call with the same sizes and pointers and replay it
@@ -78,8 +81,15 @@ typedef struct {
                          bounded-wait timeout shows in info, see the batched LU) */
     int panel_width;  /* ozlu_getrf: widest base block of the cooperative panel kernel
                          (32, 64 or 128; 0 = chosen from the rows per thread block) */
-    int reserved[9];
+    int modset;       /* p-bit calls (ozlu_mp_set_opts): OZLU_MODSET_INT8 = the 54
+                         moduli <= 255 with slice splitting (Sec. 3.2),
+                         OZLU_MODSET_EXT = the extended table of 1882 moduli
+                         <= 16191 (Sec. 4.2.4), three int8 planes per modulus */
+    int reserved[8];
 } ozlu_opts;
+
+/* Modulus tables of the p-bit Ozaki-II GEMM (ozlu_opts.modset). */
+enum { OZLU_MODSET_INT8 = 0, OZLU_MODSET_EXT = 1 };
 
 /* Plan of one Ozaki-II GEMM (Sec. 3.2 "Determining w and N"). */
 typedef struct {
@@ -118,7 +128,10 @@ int ozlu_gemm(ozlu_handle* handle, int nc, int p, int m, int n, int k, int alpha
  * Blocked LU with partial pivoting, P A = L U (Sec. 3.4, (P1)-(P4)).
  *   A      n x n expansions, overwritten by L (unit, strictly below) and U
  *   ipiv   n ints: row i was interchanged with row ipiv[i] (1-based, LAPACK)
- *   nb     panel width b (0 = 256)
+ *   nb     panel width b; 0 = measured choice among 64, 128, 256 and 512 (not
+ *          above n) on the first call for a size class (nc, p, log2 n,
+ *          back-end): the candidates factor a scratch copy of A and the
+ *          fastest is cached in the handle (ozlu_stats.tuned_nb)
  *   info   one int: 0, or the 1-based column of the first exactly zero pivot
  *          (the factorisation continues, as in LAPACK)
  * Panels (P1)-(P3) run in error-free expansion arithmetic; the trailing
@@ -144,7 +157,8 @@ int ozlu_getrs(ozlu_handle* handle, int nc, int p, int n, int nrhs,
  *   info              device array of count ints: LAPACK info per instance (0, or
  *                     the 1-based column of the first exactly zero pivot), or
  *                     -OZLU_ERR_TIMEOUT when a bounded device wait gave up
- *   nb                panel width (0 = 128)
+ *   nb                panel width (0 = the measured choice of ozlu_getrf for
+ *                     each instance's size class, made on the first call)
  * Instances run on up to 32 streams owned by the handle (joined back into the
  * handle's stream before return; the call does not wait for the GPU).  With
  * opts->graph the batch is captured into a CUDA graph on the second call with
@@ -203,6 +217,8 @@ typedef struct {
                           -e capture or instantiation failed with cudaError_t e
                           (the batch then runs eagerly on every call)        */
     double trsm_ms;
+    int last_nslice;   /* slice count S of the last residue GEMM (after autotuning) */
+    int tuned_nb;      /* panel width the last ozlu_getrf with nb = 0 used     */
 } ozlu_stats;
 int ozlu_set_timing(ozlu_handle* handle, int enable);
 int ozlu_get_stats(ozlu_handle* handle, ozlu_stats* out);
@@ -296,6 +312,27 @@ int ozlu_mp_getrf(ozlu_handle* handle, int p, int n, const ozlu_mp_matrix* A, in
  * or OZLU_ERR_CAPACITY when no S satisfies both.
  */
 int ozlu_mp_plan(int p, int k, ozlu_plan_info* out);
+
+/*
+ * Options of the handle's p-bit calls (ozlu_mp_gemm, ozlu_mp_getrf,
+ * ozlu_mp_getrs); NULL restores the defaults.  Used fields:
+ *   modset  OZLU_MODSET_INT8 (default): the 54 moduli <= 255, the smallest S
+ *           with enough capacity; OZLU_MODSET_EXT: the extended table of
+ *           Sec. 4.2.4 (moduli up to 16191, residues split into base-128
+ *           digits r = 128 q + r0 and multiplied as the three int8 planes
+ *           r0, q, r0 + q by Karatsuba), which needs far fewer GEMMs per
+ *           product (about 2x per doubling of p instead of 3x) at the cost of
+ *           O(p^2) conversion and CRT work per element
+ *   nslice  the slice count S for OZLU_MODSET_EXT (0 = the smallest feasible)
+ * Returns 0, -1 for a NULL handle, -2 for an unknown modset or nslice < 0.
+ */
+int ozlu_mp_set_opts(ozlu_handle* handle, const ozlu_opts* opts);
+
+/*
+ * The plan ozlu_mp_gemm uses with the given options (modset, nslice) for
+ * precision p and inner dimension k; host only.  moduli[] lists the first 64.
+ */
+int ozlu_mp_plan_opts(int p, int k, const ozlu_opts* opts, ozlu_plan_info* out);
 
 /* Solve A X = B from ozlu_mp_getrf's factors; B is n x nrhs (p-bit), overwritten. */
 int ozlu_mp_getrs(ozlu_handle* handle, int p, int n, int nrhs, const ozlu_mp_matrix* LU, const int* ipiv,

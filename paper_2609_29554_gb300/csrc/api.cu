@@ -1,6 +1,9 @@
 // C ABI entry points, handle and device workspace.
 #include <string.h>
 
+#include <math.h>
+
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -133,37 +136,59 @@ int plan_for(ozlu_handle* h, int p, int K, const ozlu_opts* o, const Plan** out,
 
 static size_t align_up(size_t v) { return (v + 255) / 256 * 256; }
 
-// Measured choice of the residue back-end (Sec. 3.5 guideline: the format
-// maximising bits per modulus times engine throughput, which the paper
-// concludes can only be decided by measuring at the actual size).  Each
-// feasible back-end whose model time (residue ops / engine rate) is within
-// 4x of the best model is run on the caller's operands into a scratch C
-// (once untimed, then twice timed with events, the faster counting); the
-// fastest is cached per (nc, p, k, options, log2 m, log2 n).  The first call
-// of a new shape therefore waits for the stream.
+// Measured choice of the residue back-end and the slice count (Sec. 3.5
+// guideline: the format maximising bits per modulus times engine throughput,
+// which the paper concludes can only be decided by measuring at the actual
+// size; Sec. 3.2: S balances conversion against GEMM cost).  For each
+// feasible back-end the slice counts tried are the smallest feasible S_min,
+// S_min + 1 and the cost model's S* of Eq. (Lhint) when it is larger (only
+// the caller's S when opts->nslice is set).  Every
+// candidate whose model time (residue ops / engine rate) is within 4x of the
+// best model is run on the caller's operands into a scratch C (once untimed,
+// then twice timed with events, the faster counting); the fastest (back-end,
+// S) is cached per (nc, p, k, options, log2 m, log2 n).  The first call of a
+// new shape therefore waits for the stream.
 int autotune(ozlu_handle* h, int nc, int p, int m, int n, int k, const double* A, long long lda,
-             const double* B, long long ldb, const ozlu_opts& o, int* out) {
+             const double* B, long long ldb, const ozlu_opts& o, int* be_out, int* s_out) {
     auto lg = [](int v) { int r = 0; while ((1 << r) < v) ++r; return r; };
     const auto key = std::make_tuple(nc, p, k, o.nslice * 1000000 + o.extra_groups * 1000 + o.g_ex,
                                      lg(m), lg(n));
     auto it = h->tuned.find(key);
     if (it != h->tuned.end()) {
-        *out = it->second;
+        *be_out = it->second.first;
+        *s_out = it->second.second;
         return OZLU_OK;
     }
     // engine rates in residue-product tera-ops per second (GB300 measurements)
-    const int cand[4] = {OZLU_BE_FP16, OZLU_BE_FP8, OZLU_BE_INT8, OZLU_BE_FP64};
+    // and the Eq. (Lhint) cost ratios r (the paper's 30 for INT8-class
+    // engines, 17.9 for binary64)
+    const int cand_be[4] = {OZLU_BE_FP16, OZLU_BE_FP8, OZLU_BE_INT8, OZLU_BE_FP64};
     const double rate[4] = {600.0, 1700.0 / 3.0, 150.0, 1.0};
-    double model[4];
-    bool ok[4];
+    const double rcost[4] = {30.0, 30.0, 30.0, 17.9};
+    struct Cand { int be, S; double model; };
+    std::vector<Cand> cands;
     double best_model = 1e300;
     for (int c = 0; c < 4; ++c) {
         ozlu_opts t = o;
-        t.backend = cand[c];
+        t.backend = cand_be[c];
         Plan pl;
-        ok[c] = make_plan(p, k, &t, pl) == OZLU_OK;
-        model[c] = ok[c] ? 2.0 * m * n * (double)k * pl.N * pl.pair_terms / (rate[c] * 1e12) : 1e300;
-        if (ok[c] && model[c] < best_model) best_model = model[c];
+        if (make_plan(p, k, &t, pl) != OZLU_OK) continue;
+        std::vector<int> slist{pl.S};
+        if (o.nslice == 0) {
+            const int slack = (int)ceil(log2(2.0 * k) - 1e-12) + 16 + o.g_ex;
+            const int seed = std::max(pl.S, lhint_S(rcost[c], p + slack, m, n));
+            slist = {pl.S, pl.S + 1};
+            if (seed > pl.S + 1) slist.push_back(seed);
+        }
+        for (int S : slist) {
+            ozlu_opts ts = t;
+            ts.nslice = S;
+            Plan ps;
+            if (make_plan(p, k, &ts, ps) != OZLU_OK) continue;
+            const double model = 2.0 * m * n * (double)k * ps.N * ps.pair_terms / (rate[c] * 1e12);
+            cands.push_back({cand_be[c], S, model});
+            best_model = std::min(best_model, model);
+        }
     }
     // scratch C
     const size_t cbytes = sizeof(double) * nc * (size_t)m * n;
@@ -173,13 +198,14 @@ int autotune(ozlu_handle* h, int nc, int p, int m, int n, int k, const double* A
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     float best = 1e30f;
-    int choice = OZLU_BE_INT8;
+    int choice = OZLU_BE_INT8, choice_s = 0;
     const bool timing = h->timing;
     h->timing = false;
-    for (int c = 0; c < 4; ++c) {
-        if (!ok[c] || model[c] > 4.0 * best_model) continue;
+    for (const Cand& cd : cands) {
+        if (cd.model > 4.0 * best_model) continue;
         ozlu_opts t = o;
-        t.backend = cand[c];
+        t.backend = cd.be;
+        t.nslice = cd.S;
         // an untimed first run (workspace growth, first launch of a kernel),
         // then the faster of two timed runs
         float cms = 1e30f;
@@ -198,21 +224,20 @@ int autotune(ozlu_handle* h, int nc, int p, int m, int n, int k, const double* A
             continue;
         }
         if (rc) break;
-        if (cms < best) { best = cms; choice = cand[c]; }
+        if (cms < best) { best = cms; choice = cd.be; choice_s = cd.S; }
     }
     h->timing = timing;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc && rc != OZLU_ERR_UNSUPPORTED) return rc;
-    h->tuned[key] = choice;
+    h->tuned[key] = std::make_pair(choice, choice_s);
     h->stats.last_backend = choice;
-    *out = choice;
+    *be_out = choice;
+    *s_out = choice_s;
     return OZLU_OK;
 }
 
 // The device part of one GEMM, all pointers on the device.
-int autotune(ozlu_handle* h, int nc, int p, int m, int n, int k, const double* A, long long lda,
-             const double* B, long long ldb, const ozlu_opts& o, int* out);
 
 int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, const double* A,
                 long long lda, const double* B, long long ldb, int beta, double* C,
@@ -231,8 +256,10 @@ int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, c
     memset(&o, 0, sizeof o);
     if (opts) o = *opts;
     if (o.backend == OZLU_BE_AUTO) {
-        const int rc0 = autotune(h, nc, p, m, n, k, A, lda, B, ldb, o, &o.backend);
+        int S = 0;
+        const int rc0 = autotune(h, nc, p, m, n, k, A, lda, B, ldb, o, &o.backend, &S);
         if (rc0) return rc0;
+        if (o.nslice == 0) o.nslice = S;
     }
     const Plan* pl;
     const DevTable* tab;
@@ -284,6 +311,7 @@ int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, c
     h->stats.gemm_launches += 1;
     h->stats.crt_launches += 1;
     h->stats.last_backend = be;
+    h->stats.last_nslice = pl->S;
     h->stats.gemm_ops += 2.0 * m * n * (double)k * pl->N * pl->pair_terms * P;
     h->stats.crt_bytes += (double)pl->G * pl->N * m * n + 8.0 * nc * m * n * (beta ? 2 : 1);
     h->stats.convert_bytes += 8.0 * nc * ((double)m * k + (double)k * n) +
@@ -377,9 +405,13 @@ int ozlu_destroy(ozlu_handle* h) {
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
     if (h->dev_err) cudaFree(h->dev_err);
+    for (auto& e : h->ext_plans)
+        if (e.second.dev) cudaFree(e.second.dev);
+    h->ext_plans.clear();
     h->ws.release();
     h->stage.release();
     h->tune_ws.release();
+    h->nb_ws.release();
     if (h->lu_scratch) cudaFree(h->lu_scratch);
     if (h->coop_scratch) cudaFree(h->coop_scratch);
     for (auto& e : h->pool) cudaEventDestroy(e);

@@ -203,8 +203,7 @@ extern "C" int ozlu_getrf_batched(ozlu_handle* h, int nc, int p, int count, cons
     if (!lda) return -7;
     if (!ipiv) return -8;
     if (!info || !is_device_ptr(info)) return -9;
-    if (nb == 0) nb = 128;
-    if (nb < 1) return -10;
+    if (nb < 0) return -10;
     for (int i = 0; i < count; ++i) {
         if (n[i] < 0) return -5;
         if (n[i] && (!A[i] || !is_device_ptr(A[i]))) return -6;
@@ -225,13 +224,22 @@ extern "C" int ozlu_getrf_batched(ozlu_handle* h, int nc, int p, int count, cons
         key.push_back(lda[i]);
         key.push_back((long long)ipiv[i]);
     }
+    // nb = 0: each instance takes the measured panel width of its size class
+    // (tuned on the first call, one representative instance per class)
+    std::vector<int> nbs(count, nb);
+    if (nb == 0) {
+        for (int i = 0; i < count; ++i) {
+            if (n[i] == 0) { nbs[i] = 1; continue; }
+            if ((rc = tune_nb(h, nc, p, n[i], A[i], lda[i], &o, &nbs[i]))) return rc;
+        }
+    }
     const auto lists = assign(count, n);
     // concurrent instances take fewer SMs per panel (32 rows per block at least;
     // 256 TD instances: 576 ms against 643 ms with 16); a single instance keeps 16
     for (int k = 0; k < NSUB; ++k) h->sub[k]->coop_min_rows = count > 1 ? 32 : 16;
     auto issue = [&](cudaStream_t root) -> int {
         return fork_join(h, root, lists, [&](ozlu_handle* s, int i) -> int {
-            return getrf_one(s, nc, p, n[i], A[i], lda[i], ipiv[i], nb, info + i, &o);
+            return getrf_one(s, nc, p, n[i], A[i], lda[i], ipiv[i], nbs[i], info + i, &o);
         });
     };
     return run_batched(h, key, o.graph != 0, issue);

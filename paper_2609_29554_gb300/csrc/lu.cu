@@ -18,6 +18,8 @@
 // the off-diagonal updates by the Ozaki-II GEMM.
 #include <string.h>
 
+#include <tuple>
+
 #include "expansion.cuh"
 #include "mpf.cuh"
 #include "ozlu_handle.h"
@@ -322,16 +324,22 @@ __global__ void __launch_bounds__(128) column_step_kernel(double* A, long long l
 // [c0, n).  One block per SM owns a contiguous slice of rows and keeps its
 // b-column slice in shared memory as L-limb floats for the whole block.  A
 // column step needs one exchange: each block publishes its best candidate row
-// for the column (its index, its reciprocal and the whole row) in its slot,
-// then one 64-bit word holding the column number and an ordering key of the
-// candidate; every block waits for all G stamp words (one load each when they
-// are there), reduces the same keys to the same pivot, takes the pivot row
-// from the winner's slot, swaps it into place among its rows, scales and
-// updates.  Waiting on the stamps replaces a grid barrier, and the
-// slots are double-buffered by column parity: a block can only stamp column
-// kc + 2 after every block has stamped kc + 1, i.e. after every block has
-// finished reading the slots of column kc.  The interchanges of the columns
-// outside the base block are applied once, after the last column.
+// for the column (its index and the whole row) in its slot, then one 64-bit
+// word holding the column number and an ordering key of the candidate; every
+// block waits for all G stamp words (one load each when they are there),
+// reduces the same keys to the same pivot, takes the pivot row from the
+// winner's slot, swaps it into place among its rows, scales and updates.
+// The exchange overlaps the trailing update: a block first updates only the
+// rows the next step needs from it (its next candidate and the row that the
+// pivot will replace), publishes them, and only then updates the rest of its
+// rows; meanwhile one thread forms the reciprocal of its candidate and
+// publishes it under a second stamp, which the other blocks wait for (from
+// the winner only) when they need the multipliers.  Waiting on the stamps
+// replaces a grid barrier, and the slots are double-buffered by column
+// parity: a block can only stamp column kc + 2 after every block has stamped
+// kc + 1, i.e. after every block has finished reading the slots of column kc.
+// The interchanges of the columns outside the base block are applied once,
+// after the last column.
 // Every wait is bounded (2 s of the global timer); on expiry the kernel
 // records OZLU_ERR_TIMEOUT in the scratch and every block returns.
 constexpr int COOP_MAXG = 304;           // blocks (up to 2 per SM)
@@ -347,7 +355,8 @@ constexpr unsigned long long KEY_MASK = (1ull << STAMP_SHIFT) - 1;
 
 template <int L>
 struct CoopSlot {
-    unsigned long long stamp;
+    unsigned long long stamp;      // column tag and key: idx and row are published
+    unsigned long long stamp_rec;  // column tag: rec is published
     int idx;                 // the candidate's global row index, -1 if none
     int pad;
     MPF<L> rec;              // 1 / the candidate (0 for a zero candidate)
@@ -368,7 +377,10 @@ template <int L>
 __global__ void coop_reset_kernel(CoopScratch<L>* sc) {
     const int t = threadIdx.x;
     if (t == 0) sc->error = 0;
-    if (t < 2 * COOP_MAXG) sc->part[t / COOP_MAXG][t % COOP_MAXG].stamp = 0ull;
+    if (t < 2 * COOP_MAXG) {
+        sc->part[t / COOP_MAXG][t % COOP_MAXG].stamp = 0ull;
+        sc->part[t / COOP_MAXG][t % COOP_MAXG].stamp_rec = 0ull;
+    }
 }
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -463,7 +475,7 @@ __device__ __forceinline__ void warp_best_key(unsigned long long& k, int& idx, i
 }
 
 template <int N>
-__global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
+__global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
     double* A, long long lda, int n, int c0, int b, int p0, int p1, int rows_per_block,
     int* ipiv, int* info, CoopScratch<Limbs<N>::L>* sc) {
     constexpr int L = Limbs<N>::L;
@@ -476,7 +488,6 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
     __shared__ MPF<L> prow[PBASE];  // the pivot row
     __shared__ MPF<L> otmp[PBASE];  // old row c (for the owner of the pivot row)
     __shared__ MPF<L> rec;         // 1 / pivot
-    __shared__ MPF<L> crec;        // 1 / this block's next candidate
     __shared__ MPF<L> cv;          // this block's next candidate
     __shared__ int ci, s_piv, s_widx, s_fail;
     __shared__ int s_pivs[PBASE];
@@ -493,7 +504,7 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
     __syncthreads();
 
     // warp 0: this block's best candidate in local column kc among rows >=
-    // row_lo (cv, ci) and its reciprocal (crec)
+    // row_lo (cv, ci)
     auto candidate = [&](int kc, int row_lo) {
         unsigned long long bk = 0;
         int bi = -1, aux = 0;
@@ -519,11 +530,11 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
         if (tid == 0) {
             ci = I;
             cv = I >= 0 ? a[(I - r0) * bs + kc] : mpf_make_zero<L>();
-            crec = (I >= 0 && !mpf_zero<L>(cv)) ? mpf_recip<L>(cv) : mpf_make_zero<L>();
         }
     };
     // all threads: publish the candidate of column kc (every column of its row
-    // final) and, from the owner of row c0 + kc, that row's old contents
+    // final) and, from the owner of row c0 + kc, that row's old contents;
+    // stamp A carries the key
     auto publish = [&](int kc) {
         CoopSlot<L>& slot = sc->part[kc & 1][g];
         const int wi = ci;
@@ -532,10 +543,7 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
             for (int k = tid; k < b; k += T) slot.row[k] = a[(wi - r0) * bs + k];
         if (owner(c) == g)
             for (int k = tid; k < b; k += T) sc->orow[kc & 1][k] = a[(c - r0) * bs + k];
-        if (tid == 0) {
-            slot.idx = wi;
-            slot.rec = crec;
-        }
+        if (tid == 0) slot.idx = wi;
         __syncthreads();
         if (tid == 0) {
             __threadfence();
@@ -544,13 +552,24 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
                 ((unsigned long long)((c + 1) & 0xfffff) << STAMP_SHIFT) | key;
         }
     };
+    // thread 0: the reciprocal of the candidate of column kc, then stamp B
+    auto publish_rec = [&](int kc) {
+        CoopSlot<L>& slot = sc->part[kc & 1][g];
+        const MPF<L> r = (ci >= 0 && !mpf_zero<L>(cv)) ? mpf_recip<L>(cv) : mpf_make_zero<L>();
+        slot.rec = r;
+        __threadfence();
+        *reinterpret_cast<volatile unsigned long long*>(&slot.stamp_rec) =
+            (unsigned long long)((c0 + kc + 1) & 0xfffff) << STAMP_SHIFT;
+    };
 
     if (tid < 32) candidate(0, c0);
     __syncthreads();
     publish(0);
+    if (tid == 0) publish_rec(0);
     for (int kc = 0; kc < b; ++kc) {
         const int c = c0 + kc;
-        // warp 0: wait for every stamp of column kc, reduce the keys to the pivot
+        // warp 0: wait for every stamp A of column kc, reduce the keys to the
+        // pivot, then wait for the winner's stamp B (its reciprocal)
         if (tid < 32) {
             constexpr int PER = (COOP_MAXG + 31) / 32;
             const unsigned want = (unsigned)((c + 1) & 0xfffff);
@@ -571,11 +590,12 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
                 }
                 key[u] &= KEY_MASK;
             }
-            const bool fail = __any_sync(0xffffffffu, !ok);
+            bool fail = __any_sync(0xffffffffu, !ok);
+            int W = -1;
             if (!fail) {
                 __threadfence();  // the slots' contents are visible after their stamps
                 unsigned long long K = 0;
-                int W = -1, dummy = 0;
+                int dummy = 0;
 #pragma unroll
                 for (int u = 0; u < PER; ++u) {
                     const int q = tid + 32 * u;
@@ -604,9 +624,19 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
                     warp_best<L>(v, vi, vw);
                     W = vw;
                 }
-                if (tid == 0) s_widx = W < 0 ? 0 : W;  // W >= 0: the owner of row c has a candidate
+                if (W < 0) W = 0;  // W >= 0: the owner of row c has a candidate
+                if (tid == 0) {
+                    const unsigned long long sb =
+                        wait_stamp(&sc->part[kc & 1][W].stamp_rec, want, &sc->error);
+                    s_fail = sb == 0 ? 1 : 0;
+                    if (sb) __threadfence();
+                }
+                fail = __shfl_sync(0xffffffffu, tid == 0 ? s_fail : 0, 0) != 0;
             }
-            if (tid == 0) s_fail = fail ? 1 : 0;
+            if (tid == 0) {
+                s_widx = W < 0 ? 0 : W;
+                s_fail = fail ? 1 : 0;
+            }
         }
         __syncthreads();
         if (s_fail) return;
@@ -650,20 +680,37 @@ __global__ void __launch_bounds__(COOP_THREADS) base_block_coop_kernel(
         }
         __syncthreads();
         if (cols == 0) break;
-        // lookahead: warp 0 picks the next candidate and forms its reciprocal
-        // while the other warps update the remaining columns
-        if (tid < 32) {
-            candidate(kc + 1, c + 1);
-        } else if (!zero && cols > 1) {
-            const int rest = cols - 1;
-            const int total = rows * rest;
-            for (int p = tid - 32; p < total; p += T - 32) {
-                const int r = lo + p / rest, k = kc + 2 + (p - (p / rest) * rest);
+        // warp 0: the next candidate
+        if (tid < 32) candidate(kc + 1, c + 1);
+        __syncthreads();
+        // the rows the next step reads from this block first: the candidate
+        // and (from its owner) row c + 1, which the pivot will replace
+        const int pa = ci >= 0 ? ci - r0 : -1;
+        const int pb = owner(c + 1) == g ? c + 1 - r0 : -1;
+        const int rest = cols - 1;
+        if (!zero && rest > 0) {
+            const int nprio = (pa >= 0 ? 1 : 0) + (pb >= 0 && pb != pa ? 1 : 0);
+            for (int p = tid; p < nprio * rest; p += T) {
+                const int which = p / rest, k = kc + 2 + (p - which * rest);
+                const int r = (which == 0 && pa >= 0) ? pa : pb;
                 a[r * bs + k] = mpf_fms<L>(a[r * bs + k], a[r * bs + kc], prow[k]);
             }
         }
         __syncthreads();
         publish(kc + 1);
+        // thread 0 forms and publishes the reciprocal while the other warps
+        // update the remaining rows
+        if (tid == 0) {
+            publish_rec(kc + 1);
+        } else if (tid >= 32 && !zero && rest > 0) {
+            const int total = rows * rest;
+            for (int p = tid - 32; p < total; p += T - 32) {
+                const int r = lo + p / rest, k = kc + 2 + (p - (p / rest) * rest);
+                if (r == pa || r == pb) continue;
+                a[r * bs + k] = mpf_fms<L>(a[r * bs + k], a[r * bs + kc], prow[k]);
+            }
+        }
+        __syncthreads();
     }
     for (int p = tid; p < nr * b; p += T) {
         const int r = p / b, k = p - r * b;
@@ -1169,6 +1216,9 @@ int getrf_one(ozlu_handle* h, int nc, int p, int n, double* A, long long lda, in
     int rc = lu_scratch(h, &sc);
     if (rc) return rc;
     cudaStream_t s = h->stream;
+    // the unblocked naive comparison of Sec. 3.4: b = 1, every column's
+    // rank-1 update of the whole trailing matrix in expansion arithmetic
+    if (opts && opts->native == 2) nb = 1;
     if (cudaMemsetAsync(sc, 0, sizeof(LuScratch), s)) return OZLU_ERR_CUDA;
     if ((rc = coop_reset(h, nc, s))) return rc;
     if ((rc = clear_err_word(h))) return rc;
@@ -1224,6 +1274,75 @@ int coop_reset(ozlu_handle* h, int nc, cudaStream_t s) {
     return cudaGetLastError() == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
 }
 
+// Panel width by measurement (nb = 0 in ozlu_getrf and the batched LU): the
+// candidates 64, 128, 256 and 512 (not above n) each factor a scratch copy of
+// A twice on the handle's stream, the second run timed with events (the first
+// grows workspaces and lets the back-end autotuner see the new shapes); the
+// fastest is cached per (nc, p, log2 n, back-end).  Never inside a capture.
+int tune_nb(ozlu_handle* h, int nc, int p, int n, const double* A, long long lda, const ozlu_opts* opts,
+            int* nb_out) {
+    int lgn = 0;
+    while ((1 << lgn) < n) ++lgn;
+    const int be = opts ? opts->backend : 0;
+    const auto key = std::make_tuple(nc, p, lgn, be);
+    auto it = h->tuned_nb.find(key);
+    if (it != h->tuned_nb.end()) {
+        *nb_out = it->second;
+        h->stats.tuned_nb = it->second;
+        return OZLU_OK;
+    }
+    if (n <= 64 || h->capturing) {
+        *nb_out = n <= 64 ? (n > 0 ? n : 1) : 256;
+        return OZLU_OK;
+    }
+    ozlu_opts o;
+    memset(&o, 0, sizeof o);
+    if (opts) o = *opts;
+    o.graph = 0;
+    const size_t abytes = align256(sizeof(double) * nc * (size_t)n * n);
+    int rc = h->nb_ws.ensure(abytes + align256(sizeof(int) * (size_t)n) + 256);
+    if (rc) return rc;
+    double* Ac = (double*)h->nb_ws.base;
+    int* ipv = (int*)((char*)h->nb_ws.base + abytes);
+    int* inf = (int*)((char*)ipv + align256(sizeof(int) * (size_t)n));
+    cudaStream_t s = h->stream;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    const bool timing = h->timing;
+    h->timing = false;
+    float best = 1e30f;
+    int choice = 256 < n ? 256 : n;
+    const int cands[4] = {64, 128, 256, 512};
+    for (int c = 0; c < 4 && !rc; ++c) {
+        const int nb = cands[c];
+        if (nb > n && c > 0) break;
+        for (int rep = 0; rep < 2 && !rc; ++rep) {
+            if (cudaMemcpy2DAsync(Ac, sizeof(double) * nc * n, A, sizeof(double) * nc * lda, sizeof(double) * nc * n,
+                                  n, cudaMemcpyDeviceToDevice, s) != cudaSuccess) {
+                rc = OZLU_ERR_CUDA;
+                break;
+            }
+            cudaEventRecord(e0, s);
+            rc = getrf_one(h, nc, p, n, Ac, n, ipv, nb, inf, &o);
+            cudaEventRecord(e1, s);
+            if (rc) break;
+            if (cudaEventSynchronize(e1) != cudaSuccess) { rc = OZLU_ERR_CUDA; break; }
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 1 && ms < best) { best = ms; choice = nb; }
+        }
+    }
+    h->timing = timing;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return rc;
+    h->tuned_nb[key] = choice;
+    h->stats.tuned_nb = choice;
+    *nb_out = choice;
+    return OZLU_OK;
+}
+
 // waits for the stream; OZLU_ERR_TIMEOUT if a bounded device wait gave up
 int lu_result(ozlu_handle* h, cudaStream_t s, int* result) {
     LuScratch* sc = (LuScratch*)h->lu_scratch;
@@ -1247,8 +1366,7 @@ extern "C" int ozlu_getrf(ozlu_handle* h, int nc, int p, int n, double* A, long 
     if (!A && n) return -5;
     if (lda < (n > 1 ? n : 1)) return -6;
     if (!ipiv && n) return -7;
-    if (nb == 0) nb = 256;
-    if (nb < 1) return -8;
+    if (nb < 0) return -8;
     if (!info) return -9;
     if (cudaSetDevice(h->device) != cudaSuccess) return OZLU_ERR_CUDA;
     cudaStream_t s = h->stream;
@@ -1256,8 +1374,10 @@ extern "C" int ozlu_getrf(ozlu_handle* h, int nc, int p, int n, double* A, long 
     int rc = lu_scratch(h, &sc);
     if (rc) return rc;
     const bool dA = is_device_ptr(A), dP = is_device_ptr(ipiv), dI = is_device_ptr(info);
-    if (opts && opts->graph && n > 0 && dA && dP && dI)  // graph capture and replay
+    if (opts && opts->graph && n > 0 && dA && dP && dI) {  // graph capture and replay
+        if (nb == 0 && (rc = tune_nb(h, nc, p, n, A, lda, opts, &nb))) return rc;
         return ozlu_getrf_batched(h, nc, p, 1, &n, &A, &lda, &ipiv, info, nb, opts);
+    }
     const size_t abytes = sizeof(double) * nc * (size_t)lda * (n ? n : 1);
     double* gA = A;
     int* gP = ipiv;
@@ -1270,6 +1390,8 @@ extern "C" int ozlu_getrf(ozlu_handle* h, int nc, int p, int n, double* A, long 
         }
         if (!dP) gP = (int*)((char*)h->stage.base + align256(abytes));
     }
+    if (nb == 0 && n > 0 && (rc = tune_nb(h, nc, p, n, gA, lda, opts, &nb))) return rc;
+    if (nb == 0) nb = 1;
     if ((rc = getrf_one(h, nc, p, n, gA, lda, gP, nb, &sc->result, opts))) return rc;
     int result = 0;
     if ((rc = lu_result(h, s, &result))) return rc;

@@ -85,22 +85,23 @@ __device__ __forceinline__ int mp_residue(const uint32_t (&mag)[MPD], bool neg, 
 }
 
 // (S2)+(S3): one element per thread; A side: element (r, h), B side: (h, r);
-// planes [l][t][r][h] (Rpad x Kpad; zeros in the K padding, the padded rows
-// untouched).  A threads run along r (consecutive elements of a column), B
-// threads along h.
+// planes [l][t][r][h] (Rpad x Kpad), h < Kc only: the K padding is zeroed by
+// the host beforehand and the padded rows are left untouched (they only
+// reach discarded outputs).  A threads run along r (consecutive elements of
+// a column), B threads along h.
 template <int H>
 __global__ void __launch_bounds__(256) mp_convert_kernel(MPView X, int R, int Kc, int is_b,
                                                          const int* __restrict__ shifts,
                                                          const __grid_constant__ DevTable tab, int Kpad,
                                                          int Rpad, int8_t* __restrict__ planes) {
     const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= (long long)R * Kpad) return;
-    const int r = is_b ? (int)(idx / Kpad) : (int)(idx % R);
-    const int h = is_b ? (int)(idx % Kpad) : (int)(idx / R);
+    if (idx >= (long long)R * Kc) return;
+    const int r = is_b ? (int)(idx / Kc) : (int)(idx % R);
+    const int h = is_b ? (int)(idx % Kc) : (int)(idx / R);
     const size_t plane = (size_t)Rpad * Kpad, off = (size_t)r * Kpad + h;
     const int S = tab.S, w = tab.w;
     const long long x = is_b ? (long long)h + (long long)r * X.ld : (long long)r + (long long)h * X.ld;
-    if (h >= Kc || mp_zero(X, x)) {
+    if (mp_zero(X, x)) {
         for (int l = 0; l < tab.N; ++l)
             for (int t = 0; t < S; ++t) planes[(size_t)(l * S + t) * plane + off] = 0;
         return;
@@ -139,6 +140,111 @@ __global__ void __launch_bounds__(256) mp_convert_kernel(MPView X, int R, int Kc
         }
         for (int l = 0; l < tab.N; ++l)
             planes[(size_t)(l * S + t) * plane + off] = (int8_t)mp_residue<H>(D, dneg, tab, l);
+    }
+}
+
+// (S2)+(S3) with the extended modulus table (Sec. 4.2.4).  A warp takes 32
+// consecutive positions h of one row r (A side: element (r, h); B side:
+// element (h, r)), one per lane, so that every plane byte the warp writes is
+// contiguous.  Each lane forms its S digits in turn (bits [t w, (t + 1) w)
+// of |X| plus the carry of the digit below, as mp_convert_kernel does), keeps
+// the digit's words in shared memory ([word][lane]), and takes the residue
+// modulo every m_l as sum_j word_j (2^(32 j) mod m_l), four moduli at a time;
+// the balanced digit (Eq. (2)) is applied to the residue: a digit that wraps
+// to D - 2^w (or 2^w - D for negative X) has residue +-((2^w mod m) - D mod m).
+// The centered residue r is stored as its base-128 planes r0, q, r0 + q.
+constexpr int EXT_WARPS_MAX = 4;
+
+__device__ __forceinline__ uint32_t reduce64(unsigned long long a, uint32_t m, uint32_t magic, uint32_t two32) {
+    const uint32_t hi = mod_small((uint32_t)(a >> 32), m, magic);
+    const uint32_t lo = mod_small((uint32_t)a, m, magic);
+    return mod_small(hi * two32 + lo, m, magic);
+}
+
+__global__ void mp_convert_ext_kernel(MPView X, int R, int Kc, int is_b, const int* __restrict__ shifts,
+                                      const ExtDev E, int Kpad, int Rpad, int8_t* __restrict__ planes) {
+    extern __shared__ uint32_t dsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    const int groups = (Kc + 31) / 32;  // 32-position groups per row (the K padding is zeroed by the host)
+    const long long task = (long long)blockIdx.x * nwarp + warp;
+    if (task >= (long long)R * groups) return;
+    const int r = (int)(task / groups), h = (int)(task % groups) * 32 + lane;
+    if (h >= Kc) return;
+    const int N = E.N, S = E.S, w = E.w;
+    const size_t plane = (size_t)Rpad * Kpad, off = (size_t)r * Kpad + h;
+    const long long x = is_b ? (long long)h + (long long)r * X.ld : (long long)r + (long long)h * X.ld;
+    const bool zero = mp_zero(X, x);
+    if (zero) {
+        for (int l = 0; l < N; ++l)
+            for (int t = 0; t < S; ++t)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) planes[(size_t)((l * S + t) * 3 + c) * plane + off] = 0;
+        return;
+    }
+    uint32_t* D = dsm + (size_t)warp * E.WD * 32 + lane;  // word k at D[32 k]
+    const bool neg = X.signs[x] != 0;
+    const long long sh = 32LL * X.L - X.exps[x] - shifts[r];
+    const int nw = (w + 31) >> 5;
+    uint32_t carry = 0;
+    for (int t = 0; t < S; ++t) {
+        // digit words (bits below w), the top bit w - 1 and whether the bits
+        // below it are all zero / all one
+        bool lowzero = true, lowones = true;
+        uint32_t top = 0;
+        for (int k = 0; k < nw; ++k) {
+            uint32_t v = mant32(X, x, (long long)t * w + 32 * k + sh);
+            const int hib = w - 32 * k;  // bits of this word below w
+            if (hib < 32) v &= (1u << hib) - 1u;
+            D[32 * k] = v;
+            const int lim = w - 1 - 32 * k;  // bits of this word below w - 1
+            if (lim >= 32) {
+                lowzero &= v == 0;
+                lowones &= v == 0xffffffffu;
+            } else if (lim >= 0) {
+                const uint32_t msk = lim ? (1u << lim) - 1u : 0u;
+                lowzero &= (v & msk) == 0;
+                lowones &= (v & msk) == msk;
+                top = (v >> lim) & 1u;
+            }
+        }
+        bool wrap = false;
+        if (t < S - 1) {
+            const bool ge = top || (carry && lowones);
+            const bool half = carry ? (!top && lowones) : (top && lowzero);
+            wrap = neg ? (ge && !half) : ge;
+        }
+        const bool dneg = wrap ? !neg : neg;
+        for (int l0 = 0; l0 < N; l0 += 4) {
+            unsigned long long acc[4] = {0ull, 0ull, 0ull, 0ull};
+            const int cnt = min(4, N - l0);
+            for (int k = 0; k < nw; ++k) {
+                const unsigned long long dv = D[32 * k];
+                const uint32_t* pk = E.pow32 + (size_t)k * N + l0;
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (q < cnt) acc[q] += dv * pk[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                if (q >= cnt) break;
+                const int l = l0 + q;
+                const uint32_t m = (uint32_t)E.mod[l], mg = E.magic[l];
+                uint32_t v = reduce64(acc[q], m, mg, E.two32[l]);
+                v = mod_small(v + carry, m, mg);
+                if (wrap) v = mod_small(E.pw[l] + m - v, m, mg);
+                if (dneg && v) v = m - v;
+                int c = (int)v;
+                if (c > (int)(m - 1) / 2) c -= (int)m;
+                int qd = (abs(c) + 63) >> 7;
+                if (c < 0) qd = -qd;
+                const int r0 = c - 128 * qd;
+                int8_t* dst = planes + (size_t)((l * S + t) * 3) * plane + off;
+                dst[0] = (int8_t)r0;
+                dst[plane] = (int8_t)qd;
+                dst[2 * plane] = (int8_t)(r0 + qd);
+            }
+        }
+        carry = wrap ? 1u : 0u;
     }
 }
 
@@ -191,6 +297,72 @@ __device__ void acc_add_mp(const Acc& A, const MPView& C, long long x, long long
         c = t >> 32;
     }
 }
+
+// P_int (two's complement, NW words in A) on the grid 2^(w g0 - mu_i - nu_j):
+// the fused update with the old C and the single rounding to p bits (S6)
+__device__ void mp_finish(const Acc& A, int NW, long long E, int alpha, int beta, const MPView& C, long long xc,
+                          int p) {
+    bool neg = (A[NW - 1] >> 31) != 0;
+    if (neg) acc_negate(A);
+    if (alpha < 0) neg = !neg;
+    if (beta && !mp_zero(C, xc)) {
+        const int ctop = C.exps[xc];
+        const int Lp = acc_bitlen(A);
+        const long long etop = max(E + Lp, (long long)ctop) + 1;
+        const long long Wb = 32LL * NW - 2;
+        if (etop - E > Wb) {
+            const long long E2 = etop - Wb;
+            acc_shr(A, (int)(E2 - E));  // truncation toward zero of the product
+            E = E2;
+        }
+        if (neg) acc_negate(A);
+        // trunc(C 2^-E): magnitude bit b at bit b + (exps - 32 L) - E of the grid
+        acc_add_mp(A, C, xc, (long long)C.exps[xc] - 32LL * C.L - E, C.signs[xc] != 0);
+        neg = (A[NW - 1] >> 31) != 0;
+        if (neg) acc_negate(A);
+    }
+    // round |total| 2^E to p bits and store
+    const int Lt = acc_bitlen(A);
+    if (Lt == 0) {
+        for (int k = 0; k < C.L; ++k) C.limbs[(long long)k * C.plane + xc] = 0;
+        C.exps[xc] = 0;
+        C.signs[xc] = 0;
+        return;
+    }
+    int Lo = Lt;
+    if (Lt > p) {
+        const int sh = Lt - p;
+        const bool rb = (acc_bits32(A, sh - 1) & 1u) != 0;
+        bool sticky = false;
+        for (int k = 0; k < NW && 32 * k < sh - 1; ++k) {
+            const int lo = 32 * k, hiw = min(32 * k + 32, sh - 1);
+            const uint32_t mask = hiw - lo >= 32 ? 0xffffffffu : ((1u << (hiw - lo)) - 1u);
+            sticky |= (A[k] & mask) != 0;
+        }
+        const bool up = rb && (sticky || (acc_bits32(A, sh) & 1u));
+        // clear the bits below sh, then add 2^sh if rounding up
+        for (int k = 0; k < NW; ++k) {
+            if (32 * k + 32 <= sh) A[k] = 0;
+            else if (32 * k < sh) A[k] &= ~((1u << (sh - 32 * k)) - 1u);
+        }
+        if (up) {
+            uint64_t c = 0;
+            for (int k = sh >> 5; k < NW; ++k) {
+                const uint64_t add = (k == (sh >> 5)) ? (1ull << (sh & 31)) : 0ull;
+                const uint64_t t = (uint64_t)A[k] + add + c;
+                A[k] = (uint32_t)t;
+                c = t >> 32;
+                if (k > (sh >> 5) && !c) break;
+            }
+            Lo = acc_bitlen(A);
+        }
+    }
+    const long long first = (long long)Lo - 32LL * C.L;  // bit of A at limb 0, bit 0
+    for (int k = 0; k < C.L; ++k) C.limbs[(long long)k * C.plane + xc] = acc_bits32(A, first + 32LL * k);
+    C.exps[xc] = (int)(Lo + E);
+    C.signs[xc] = neg ? 1 : 0;
+}
+
 
 template <int WG>
 __global__ void __launch_bounds__(MPCT) mp_crt_kernel(const uint8_t* __restrict__ T, int m, int nchunk, int j0,
@@ -251,75 +423,94 @@ __global__ void __launch_bounds__(MPCT) mp_crt_kernel(const uint8_t* __restrict_
         win[WG] += r ? (long long)((int)Sg[WG - 1] >> (32 - r)) : ((Sg[WG - 1] >> 31) ? -1LL : 0LL);
     }
     while (base < NW) retire();
-    // P_int (two's complement, NW words) on the grid 2^E
-    bool neg = (A[NW - 1] >> 31) != 0;
-    if (neg) acc_negate(A);
-    if (alpha < 0) neg = !neg;
-    long long E = (long long)tab.w * tab.g0 - mu[i] - nu[j];
-    const long long xc = (long long)i + (long long)j * C.ld;
-    if (beta && !mp_zero(C, xc)) {
-        const int ctop = C.exps[xc];
-        const int Lp = acc_bitlen(A);
-        const long long etop = max(E + Lp, (long long)ctop) + 1;
-        const long long Wb = 32LL * NW - 2;
-        if (etop - E > Wb) {
-            const long long E2 = etop - Wb;
-            acc_shr(A, (int)(E2 - E));  // truncation toward zero of the product
-            E = E2;
-        }
-        if (neg) acc_negate(A);
-        // trunc(C 2^-E): magnitude bit b at bit b + (exps - 32 L) - E of the grid
-        acc_add_mp(A, C, xc, (long long)C.exps[xc] - 32LL * C.L - E, C.signs[xc] != 0);
-        neg = (A[NW - 1] >> 31) != 0;
-        if (neg) acc_negate(A);
-    }
-    // round |total| 2^E to p bits and store
-    const int Lt = acc_bitlen(A);
-    if (Lt == 0) {
-        for (int k = 0; k < C.L; ++k) C.limbs[(long long)k * C.plane + xc] = 0;
-        C.exps[xc] = 0;
-        C.signs[xc] = 0;
-        return;
-    }
-    int Lo = Lt;
-    if (Lt > p) {
-        const int sh = Lt - p;
-        const bool rb = (acc_bits32(A, sh - 1) & 1u) != 0;
-        bool sticky = false;
-        for (int k = 0; k < NW && 32 * k < sh - 1; ++k) {
-            const int lo = 32 * k, hiw = min(32 * k + 32, sh - 1);
-            const uint32_t mask = hiw - lo >= 32 ? 0xffffffffu : ((1u << (hiw - lo)) - 1u);
-            sticky |= (A[k] & mask) != 0;
-        }
-        const bool up = rb && (sticky || (acc_bits32(A, sh) & 1u));
-        // clear the bits below sh, then add 2^sh if rounding up
-        for (int k = 0; k < NW; ++k) {
-            if (32 * k + 32 <= sh) A[k] = 0;
-            else if (32 * k < sh) A[k] &= ~((1u << (sh - 32 * k)) - 1u);
-        }
-        if (up) {
-            uint64_t c = 0;
-            for (int k = sh >> 5; k < NW; ++k) {
-                const uint64_t add = (k == (sh >> 5)) ? (1ull << (sh & 31)) : 0ull;
-                const uint64_t t = (uint64_t)A[k] + add + c;
-                A[k] = (uint32_t)t;
-                c = t >> 32;
-                if (k > (sh >> 5) && !c) break;
+    mp_finish(A, NW, (long long)tab.w * tab.g0 - mu[i] - nu[j], alpha, beta, C, (long long)i + (long long)j * C.ld, p);
+}
+
+// (S5)+(S6) with the extended table: one thread per output.  For each digit
+// group, F = sum t_l / m_l in 40-bit fixed point gives R = round(F) (Eq. (11);
+// the error, below N 2^-27, cannot move F across the rounding boundary, which
+// the plan keeps 2^-5 away), and S_g = sum t_l M_l - R P modulo 2^(32 WG) is
+// formed XCH words at a time (one pass over the t values per chunk) and added
+// at bit w (g - g0) of the NW-word accumulator; then the fused update and the
+// rounding of mp_finish.
+constexpr int XCH = 8;
+
+__global__ void __launch_bounds__(MPCT) mp_crt_ext_kernel(const uint16_t* __restrict__ T, int m, int nchunk, int j0,
+                                                          const int* __restrict__ mu, const int* __restrict__ nu,
+                                                          const ExtDev E, int NW, int alpha, int beta, MPView C,
+                                                          int p) {
+    extern __shared__ uint32_t accsm[];
+    const long long e = (long long)blockIdx.x * MPCT + threadIdx.x;
+    const long long mn = (long long)m * nchunk;
+    if (e >= mn) return;
+    const int i = (int)(e % m), jj = (int)(e / m), j = j0 + jj;
+    const Acc A{accsm + threadIdx.x, NW};
+    for (int k = 0; k < NW; ++k) A[k] = 0;
+    const int N = E.N, WG = E.WG;
+    for (int gi = 0; gi < E.G; ++gi) {
+        const uint16_t* tp = T + (size_t)gi * N * mn + e;
+        unsigned long long f = 0;
+        for (int l = 0; l < N; ++l) f += (unsigned long long)tp[(size_t)l * mn] * E.inv40[l];
+        const unsigned long long R = (f + (1ull << 39)) >> 40;
+        const long long pos = (long long)E.w * gi;
+        const int q0 = (int)(pos >> 5), sr = (int)(pos & 31);
+        long long cy = 0;            // carry between the word sums of S_g (signed)
+        uint32_t prev = 0;           // previous word of S_g (funnel shift by sr)
+        unsigned long long ca = 0;   // carry of the addition into A
+        for (int c0 = 0; c0 < WG; c0 += XCH) {
+            const int cn = min(XCH, WG - c0);
+            unsigned long long a[XCH];
+#pragma unroll
+            for (int q = 0; q < XCH; ++q) a[q] = 0;
+            for (int l = 0; l < N; ++l) {
+                const unsigned long long t = tp[(size_t)l * mn];
+                const uint32_t* mw = E.Mw + (size_t)c0 * N + l;
+#pragma unroll
+                for (int q = 0; q < XCH; ++q)
+                    if (q < cn) a[q] += t * mw[(size_t)q * N];
             }
-            Lo = acc_bitlen(A);
+#pragma unroll
+            for (int q = 0; q < XCH; ++q) {
+                if (q >= cn) break;
+                const long long v = (long long)a[q] + cy - (long long)(R * E.Pw[c0 + q]);
+                const uint32_t word = (uint32_t)v;
+                cy = v >> 32;  // arithmetic
+                const uint32_t sw = sr ? (word << sr) | (prev >> (32 - sr)) : word;
+                prev = word;
+                const int idx = q0 + c0 + q;
+                if (idx < NW) {
+                    const unsigned long long sum = (unsigned long long)A[idx] + sw + ca;
+                    A[idx] = (uint32_t)sum;
+                    ca = sum >> 32;
+                }
+            }
+        }
+        // the bits of the top word shifted out, then the sign extension of S_g
+        const uint32_t sext = (prev >> 31) ? 0xffffffffu : 0u;
+        for (int idx = q0 + WG; idx < NW; ++idx) {
+            const uint32_t add = idx == q0 + WG ? (sr ? (sext << sr) | (prev >> (32 - sr)) : sext) : sext;
+            const unsigned long long sum = (unsigned long long)A[idx] + add + ca;
+            A[idx] = (uint32_t)sum;
+            ca = sum >> 32;
         }
     }
-    const long long first = (long long)Lo - 32LL * C.L;  // bit of A at limb 0, bit 0
-    for (int k = 0; k < C.L; ++k) C.limbs[(long long)k * C.plane + xc] = acc_bits32(A, first + 32LL * k);
-    C.exps[xc] = (int)(Lo + E);
-    C.signs[xc] = neg ? 1 : 0;
+    mp_finish(A, NW, (long long)E.w * E.g0 - mu[i] - nu[j], alpha, beta, C, (long long)i + (long long)j * C.ld, p);
+}
+
+// zero the K padding [Kc, Kpad) of every row of `count` planes (one 2-D
+// memset: all rows of all planes are Kpad bytes apart; the padded rows'
+// padding is zeroed too, which they do not need)
+void zero_k_padding(int8_t* planes, long long count, int R, int Rpad, int Kc, int Kpad, cudaStream_t s) {
+    if (Kc >= Kpad || R == 0) return;
+    cudaMemset2DAsync(planes + Kc, Kpad, 0, Kpad - Kc, (size_t)count * Rpad, s);
 }
 
 template <int H>
 void convert_h(const MPView& X, int R, int Kc, int is_b, const int* shifts, const DevTable& tab, int Kpad, int Rpad,
                int8_t* planes, cudaStream_t s) {
     // rows [0, R) only (padded rows reach discarded outputs); zeros in the K padding
-    const long long total = (long long)R * Kpad;
+    zero_k_padding(planes, (long long)tab.N * tab.S, R, Rpad, Kc, Kpad, s);
+    const long long total = (long long)R * Kc;
     if (total == 0) return;
     mp_convert_kernel<H><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, R, Kc, is_b, shifts, tab, Kpad, Rpad,
                                                                          planes);
@@ -379,17 +570,138 @@ int mp_plan_for(ozlu_handle* h, int p, int K, const Plan** pl, const DevTable** 
     return OZLU_OK;
 }
 
+// extended-table plan for (p, K, S) with its device tables (built once per handle)
+int mp_ext_plan_for(ozlu_handle* h, int p, int K, int S, const Plan** pl, ExtDev* dev) {
+    const auto key = std::make_tuple(p, K, S);
+    auto it = h->ext_plans.find(key);
+    if (it == h->ext_plans.end()) {
+        ozlu_handle::ExtPlan e;
+        int rc = make_plan_mp_ext(p, K, S, e.plan);
+        if (rc) return rc;
+        ExtImage img;
+        build_ext_image(e.plan, img);
+        if (!dev_alloc(&e.dev, img.words.size() * 4)) return OZLU_ERR_NOMEM;
+        if (cudaMemcpy(e.dev, img.words.data(), img.words.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaFree(e.dev);
+            return OZLU_ERR_CUDA;
+        }
+        const uint32_t* b = (const uint32_t*)e.dev;
+        ExtDev& d = e.view;
+        d.N = e.plan.N; d.S = e.plan.S; d.w = e.plan.w; d.g0 = e.plan.g0; d.G = e.plan.G;
+        d.WG = e.plan.WG; d.WD = img.WD;
+        d.mod = (const int*)(b + img.o_mod);
+        d.y = b + img.o_y;
+        d.magic = b + img.o_magic;
+        d.coef = b + img.o_coef;
+        d.pw = b + img.o_pw;
+        d.two32 = b + img.o_two32;
+        d.inv40 = (const unsigned long long*)(b + img.o_inv40);
+        d.pow32 = b + img.o_pow32;
+        d.Mw = b + img.o_Mw;
+        d.Pw = b + img.o_Pw;
+        it = h->ext_plans.emplace(key, e).first;
+    }
+    *pl = &it->second.plan;
+    *dev = it->second.view;
+    return OZLU_OK;
+}
+
+void mp_convert_ext(const MPView& X, int R, int Kc, int is_b, const int* shifts, const ExtDev& E, int Kpad, int Rpad,
+                    int8_t* planes, cudaStream_t s) {
+    zero_k_padding(planes, (long long)E.N * E.S * 3, R, Rpad, Kc, Kpad, s);
+    const long long tasks = (long long)R * ((Kc + 31) / 32);
+    if (tasks == 0) return;
+    int warps = EXT_WARPS_MAX;
+    while (warps > 1 && (size_t)warps * E.WD * 32 * 4 > 200 * 1024) warps /= 2;
+    const size_t smem = (size_t)warps * E.WD * 32 * 4;
+    raise_smem_limit((const void*)mp_convert_ext_kernel, (int)smem);
+    mp_convert_ext_kernel<<<(unsigned)((tasks + warps - 1) / warps), 32 * warps, smem, s>>>(X, R, Kc, is_b, shifts, E,
+                                                                                           Kpad, Rpad, planes);
+}
+
+// the extended-table route of mp_gemm_device
+int mp_gemm_ext(ozlu_handle* h, int p, int S, int m, int n, int k, int alpha, const ozlu_mp_matrix& A,
+                const ozlu_mp_matrix& B, int beta, const ozlu_mp_matrix& C) {
+    const Plan* pl;
+    ExtDev E;
+    int rc = mp_ext_plan_for(h, p, k, S, &pl, &E);
+    if (rc) return rc;
+    cudaStream_t s = h->stream;
+    const int Kpad = (k + 63) / 64 * 64, Mpad = (m + 127) / 128 * 128;
+    const size_t planesN = (size_t)pl->N * pl->S * 3;
+    // column chunk: t values of one chunk below 4 GiB and B planes below 2 GiB
+    const size_t tcol = (size_t)pl->G * pl->N * m * 2;
+    long long nch = (long long)(((size_t)4 << 30) / (tcol ? tcol : 1));
+    const long long bcap = (long long)(((size_t)2 << 30) / (planesN * Kpad)) / 128 * 128;
+    if (nch > bcap) nch = bcap;
+    nch = nch / 128 * 128;
+    if (nch < 128) nch = 128;
+    if (nch > n) nch = n;
+    const int Ncpad = (int)((nch + 127) / 128 * 128);
+    size_t off = 0;
+    const size_t o_mu = off; off = up256(off + sizeof(int) * (size_t)m);
+    const size_t o_nu = off; off = up256(off + sizeof(int) * (size_t)n);
+    const size_t o_ra = off; off = up256(off + planesN * Mpad * Kpad);
+    const size_t o_rb = off; off = up256(off + planesN * (size_t)Ncpad * Kpad);
+    const size_t o_t = off;  off = up256(off + tcol * (size_t)nch);
+    if ((rc = h->ws.ensure(off))) return rc;
+    char* base = (char*)h->ws.base;
+    int* mu = (int*)(base + o_mu);
+    int* nu = (int*)(base + o_nu);
+    int8_t* RA = (int8_t*)(base + o_ra);
+    int8_t* RB = (int8_t*)(base + o_rb);
+    uint16_t* T = (uint16_t*)(base + o_t);
+    const MPView vA = view_of(A, 0), vB = view_of(B, 0), vC = view_of(C, 0);
+    const int NW = mp_window_words(*pl);
+    const size_t crt_smem = sizeof(uint32_t) * (size_t)NW * MPCT;
+    if (crt_smem > 227 * 1024) return OZLU_ERR_CAPACITY;
+    raise_smem_limit((const void*)mp_crt_ext_kernel, (int)crt_smem);
+    DevTable tab;
+    memset(&tab, 0, sizeof tab);
+    const int prev = h->open_phase;
+    h->phase(PH_CONVERT);
+    mp_shift_kernel<<<(m + 127) / 128, 128, 0, s>>>(vA, m, k, 0, pl->Q, mu);
+    mp_shift_kernel<<<(n + 127) / 128, 128, 0, s>>>(vB, n, k, 1, pl->Q, nu);
+    mp_convert_ext(vA, m, k, 0, mu, E, Kpad, Mpad, RA, s);
+    h->count(3);
+    for (long long j0 = 0; j0 < n; j0 += nch) {
+        const int nc = (int)(n - j0 < nch ? n - j0 : nch);
+        const int ncp = (nc + 127) / 128 * 128;
+        h->phase(PH_CONVERT);
+        mp_convert_ext(view_of(B, j0 * B.ld), nc, k, 1, nu + j0, E, Kpad, ncp, RB, s);
+        h->phase(PH_GEMM);
+        launch_gemm_imma_ext(RA, RB, m, nc, Mpad, ncp, Kpad, tab, E, T, s);
+        h->phase(PH_CRT);
+        const long long mn = (long long)m * nc;
+        mp_crt_ext_kernel<<<(unsigned)((mn + MPCT - 1) / MPCT), MPCT, crt_smem, s>>>(T, m, nc, (int)j0, mu, nu, E,
+                                                                                     NW, alpha, beta, vC, p);
+        h->count(3);
+        h->stats.gemm_launches += 1;
+        h->stats.crt_launches += 1;
+        h->stats.gemm_ops += 2.0 * m * nc * (double)k * pl->N * pl->pair_terms * 3;
+    }
+    h->phase(prev);
+    return cudaGetLastError() == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
+}
+
 // C = beta C + alpha A B, device views (m x k, k x n, m x n)
 int mp_gemm_device(ozlu_handle* h, int p, int m, int n, int k, int alpha, const ozlu_mp_matrix& A,
                    const ozlu_mp_matrix& B, int beta, const ozlu_mp_matrix& C) {
     if (m == 0 || n == 0) return OZLU_OK;
+    if (h->mp_opts.modset == OZLU_MODSET_EXT)
+        return mp_gemm_ext(h, p, h->mp_opts.nslice, m, n, k, alpha, A, B, beta, C);
     const Plan* pl;
     const DevTable* tab;
     int rc = mp_plan_for(h, p, k, &pl, &tab);
     if (rc) return rc;
     cudaStream_t s = h->stream;
-    const int Kpad = pl->Kpad, Mpad = (m + 127) / 128 * 128;
+    // residue planes padded in K to a multiple of the GEMM's K step (64),
+    // not of the plan's 128, so that narrow products stay narrow
+    const int Kpad = (k + 63) / 64 * 64, Mpad = (m + 127) / 128 * 128;
     const size_t planesN = (size_t)pl->N * pl->S;
+    // n <= 16: 128 x 16 tiles and B planes of 16 rows
+    const bool narrow = n <= 16;
+    const int rowq = narrow ? 16 : 128;
     // column chunk: t values of one chunk below 4 GiB and B planes below 2 GiB
     const size_t tcol = (size_t)pl->G * pl->N * m;
     long long nch = (long long)(((size_t)4 << 30) / (tcol ? tcol : 1));
@@ -398,7 +710,7 @@ int mp_gemm_device(ozlu_handle* h, int p, int m, int n, int k, int alpha, const 
     nch = nch / 128 * 128;
     if (nch < 128) nch = 128;
     if (nch > n) nch = n;
-    const int Ncpad = (int)((nch + 127) / 128 * 128);
+    const int Ncpad = (int)((nch + rowq - 1) / rowq * rowq);
     size_t off = 0;
     const size_t o_mu = off; off = up256(off + sizeof(int) * (size_t)m);
     const size_t o_nu = off; off = up256(off + sizeof(int) * (size_t)n);
@@ -422,11 +734,14 @@ int mp_gemm_device(ozlu_handle* h, int p, int m, int n, int k, int alpha, const 
     h->count(3);
     for (long long j0 = 0; j0 < n; j0 += nch) {
         const int nc = (int)(n - j0 < nch ? n - j0 : nch);
-        const int ncp = (nc + 127) / 128 * 128;
+        const int ncp = (nc + rowq - 1) / rowq * rowq;
         h->phase(PH_CONVERT);
         mp_convert(view_of(B, j0 * B.ld), nc, k, 1, nu + j0, *tab, Kpad, ncp, RB, s);
         h->phase(PH_GEMM);
-        launch_gemm_imma(RA, RB, m, nc, Mpad, ncp, Kpad, *tab, T, s);
+        if (narrow)
+            launch_gemm_imma_narrow(RA, RB, m, nc, Mpad, ncp, Kpad, *tab, T, s);
+        else
+            launch_gemm_imma(RA, RB, m, nc, Mpad, ncp, Kpad, *tab, T, s);
         h->phase(PH_CRT);
         mp_crt(T, m, nc, (int)j0, mu, nu, *tab, NW, alpha, beta, vC, p, s);
         h->count(3);
@@ -451,6 +766,17 @@ bool mp_valid(const ozlu_mp_matrix* M, int p, int rows, int cols) {
     return is_device_ptr(M->limbs) && is_device_ptr(M->exps) && is_device_ptr(M->signs);
 }
 }  // namespace
+
+extern "C" int ozlu_mp_set_opts(ozlu_handle* h, const ozlu_opts* opts) {
+    if (!h) return -1;
+    if (!opts) {
+        memset(&h->mp_opts, 0, sizeof h->mp_opts);
+        return OZLU_OK;
+    }
+    if (opts->modset < 0 || opts->modset > OZLU_MODSET_EXT || opts->nslice < 0) return -2;
+    h->mp_opts = *opts;
+    return OZLU_OK;
+}
 
 extern "C" int ozlu_mp_gemm(ozlu_handle* h, int p, int m, int n, int k, int alpha, const ozlu_mp_matrix* A,
                             const ozlu_mp_matrix* B, int beta, const ozlu_mp_matrix* C) {

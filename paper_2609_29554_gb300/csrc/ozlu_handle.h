@@ -38,7 +38,10 @@ struct ozlu_handle {
     ozlu::Workspace ws;     // GEMM intermediates
     ozlu::Workspace stage;  // host-argument staging
     ozlu::Workspace tune_ws;  // scratch output of the back-end autotuner
-    std::map<std::tuple<int, int, int, int, int, int>, int> tuned;  // shape key -> back-end
+    // shape key -> (back-end, slice count) chosen by the autotuner
+    std::map<std::tuple<int, int, int, int, int, int>, std::pair<int, int>> tuned;
+    std::map<std::tuple<int, int, int, int>, int> tuned_nb;  // (nc, p, log2 n, backend) -> nb
+    ozlu::Workspace nb_ws;  // scratch copy of A for the panel-width autotuner
     std::map<std::tuple<int, int, int, int, int, int>, ozlu::PlanEntry> plans;
     ozlu::GemmLayout last;
     int* dev_err = nullptr;  // device error word of the tensor-core GEMMs
@@ -70,6 +73,15 @@ struct ozlu_handle {
     };
     std::map<std::vector<long long>, Graph> graphs;
     std::map<std::vector<long long>, int> warm;
+    // p-bit calls: options (modulus table, slice count) and the device tables
+    // of extended-table plans, keyed by (p, K, S)
+    ozlu_opts mp_opts = {};
+    struct ExtPlan {
+        ozlu::Plan plan;
+        void* dev = nullptr;
+        ozlu::ExtDev view;
+    };
+    std::map<std::tuple<int, int, int>, ExtPlan> ext_plans;
 };
 
 enum { PH_CONVERT = 0, PH_GEMM = 1, PH_CRT = 2, PH_PANEL = 3, PH_OTHER = 4, PH_TRSM = 5 };
@@ -77,6 +89,8 @@ enum { PH_CONVERT = 0, PH_GEMM = 1, PH_CRT = 2, PH_PANEL = 3, PH_OTHER = 4, PH_T
 namespace ozlu {
 int getrf_one(ozlu_handle* h, int nc, int p, int n, double* A, long long lda, int* ipiv, int nb, int* info_out,
               const ozlu_opts* opts);
+int tune_nb(ozlu_handle* h, int nc, int p, int n, const double* A, long long lda, const ozlu_opts* opts,
+            int* nb_out);
 int getrs_one(ozlu_handle* h, int nc, int p, int n, int nrhs, const double* LU, long long lda, const int* ipiv,
               double* B, long long ldb, const ozlu_opts* opts);
 int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, const double* A,

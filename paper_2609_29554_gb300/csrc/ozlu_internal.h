@@ -29,6 +29,27 @@ struct Plan {
     std::vector<uint32_t> P;               // P = prod m_l, little-endian words
     std::vector<std::vector<uint32_t>> M;  // M_l = P / m_l
     int sbar_bits = 0, WG = 0, pint_bits = 0, WX = 0, H = 0;
+    // extended modulus table (Sec. 4.2.4): the moduli and y_l of all N
+    // entries (mod[] / y[] hold at most MAXMOD), three int8 planes each
+    bool ext = false;
+    std::vector<int> ext_mod, ext_y;
+};
+
+// Constant tables of an extended-table plan, in device memory (too large for
+// a kernel parameter); word-indexed arrays are [word][modulus] so that the
+// lanes of a warp, one modulus each, read consecutive addresses.
+struct ExtDev {
+    int N, S, w, g0, G, WG, WD;
+    const int* mod;                    // [N]
+    const uint32_t* y;                 // [N]  M_l^-1 mod m_l
+    const uint32_t* magic;             // [N]  ceil(2^32 / m_l)
+    const uint32_t* coef;              // [3][N] plane weights mod m_l: 1 - 128, 16384 - 128, 128
+    const uint32_t* pw;                // [N]  2^w mod m_l
+    const uint32_t* two32;             // [N]  2^32 mod m_l
+    const unsigned long long* inv40;   // [N]  round(2^40 / m_l)
+    const uint32_t* pow32;             // [WD][N] 2^(32 j) mod m_l
+    const uint32_t* Mw;                // [WG][N] word j of M_l
+    const uint32_t* Pw;                // [WG]    word j of P
 };
 
 // Constant table of one plan, passed to kernels by value (__grid_constant__).
@@ -53,7 +74,20 @@ void raise_smem_limit(const void* kernel, int bytes);
 int device_sms();
 
 int make_plan(int p, int K, const ozlu_opts* o, Plan& out);
+// Eq. (Lhint) cost-model slice count (the autotuner's seed)
+int lhint_S(double r, int t, int M, int N);
 int make_plan_mp(int p, int K, Plan& out);  // p-bit multi-limb inputs, INT8
+// p-bit inputs with the extended modulus table (Sec. 4.2.4): S = S_req, or
+// the smallest feasible S when S_req = 0
+int make_plan_mp_ext(int p, int K, int S_req, Plan& out);
+// host image of an extended plan's device tables: the word arrays in the
+// order of ExtDev (offsets in 32-bit words, 64-word aligned)
+struct ExtImage {
+    std::vector<uint32_t> words;
+    size_t o_mod, o_y, o_magic, o_coef, o_pw, o_two32, o_inv40, o_pow32, o_Mw, o_Pw;
+    int WD;
+};
+void build_ext_image(const Plan& pl, ExtImage& img);
 void fill_table(const Plan& pl, DevTable& t);
 // the allocation-free GEMM's planner: the INT8 plan straight into a table,
 // fixed-size arrays only (no host allocation)
@@ -80,6 +114,14 @@ int launch_gemm_tc05(bool fp8, const void* RA, const void* RB, int m, int n, int
 void launch_gemm_imma(const int8_t* RA, const int8_t* RB, int m, int n, int Mpad,
                       int Npad, int Kpad, const DevTable& tab, uint8_t* T,
                       cudaStream_t s);
+// the same for n <= 16 outputs per column block: 128 x 16 tiles, B planes with
+// Npad = n rounded up to 16 rows
+void launch_gemm_imma_narrow(const int8_t* RA, const int8_t* RB, int m, int n, int Mpad, int Npad, int Kpad,
+                             const DevTable& tab, uint8_t* T, cudaStream_t s);
+// (S4)+(S5 t_l) with the extended table: three int8 Karatsuba planes per
+// modulus (plane (l, t, c) at (l S + t) 3 + c), 16-bit t values T[gi][l][j][i]
+void launch_gemm_imma_ext(const int8_t* RA, const int8_t* RB, int m, int n, int Mpad, int Npad, int Kpad,
+                          const DevTable& tab, const ExtDev& ext, uint16_t* T, cudaStream_t s);
 // (S4) binary64 residue GEMMs; t values as 32-bit words
 void launch_gemm_f64(const double* RA, const double* RB, int m, int n, int Mpad, int Npad, int Kpad,
                      const DevTable& tab, uint32_t* T, cudaStream_t s);

@@ -90,6 +90,17 @@ int ceil_log2(double v) { return (int)ceil(log2(v) - 1e-12); }
 
 }  // namespace
 
+// Eq. (Lhint): the cost-model estimate of the slice count,
+// S* = ceil(sqrt(r n_d (M + N) / (M N))), n_d = ceil(t / 16), with r the ratio
+// of per-digit residue cost to per-flop GEMM cost (30 for INT8, 17.9 for
+// binary64 in the paper) and t the width of one unsplit pass (p + slack)
+int lhint_S(double r, int t, int M, int N) {
+    if (M < 1 || N < 1 || t < 1) return 1;
+    const double nd = (double)((t + 15) / 16);
+    const int s = (int)ceil(sqrt(r * nd * ((double)M + N) / ((double)M * N)) - 1e-12);
+    return s < 1 ? 1 : s;
+}
+
 int make_plan(int p, int K, const ozlu_opts* o, Plan& out) {
     ozlu_opts d;
     memset(&d, 0, sizeof d);
@@ -199,6 +210,124 @@ int make_plan_mp(int p, int K, Plan& out) {
     return OZLU_ERR_CAPACITY;
 }
 
+namespace {
+// Sec. 4.2.4: the 54 INT8 moduli and the primes in (255, 16191], descending
+const std::vector<int>& ext_set() {
+    static const std::vector<int> ms = [] {
+        std::vector<int> v = int8_set();
+        for (int q = 257; q <= 16191; q += 2)
+            if (is_prime(q)) v.push_back(q);
+        std::sort(v.begin(), v.end(), [](int a, int b) { return a > b; });
+        return v;
+    }();
+    return ms;
+}
+}  // namespace
+
+// The rule of Sec. 3.2 with the extended table of Sec. 4.2.4: the moduli are
+// taken from the 1882-entry table (largest first), every modulus costs three
+// int8 Karatsuba planes whose products are bounded like INT8 residues
+// (|r0|, |q|, |r0 + q| <= 127), so the accumulator condition is unchanged.
+int make_plan_mp_ext(int p, int K, int S_req, Plan& out) {
+    if (p < 1 || K < 1 || S_req < 0) return OZLU_ERR_CAPACITY;
+    const int slack = ceil_log2(2.0 * K) + 16;
+    const int Kpad = (K + 127) / 128 * 128;
+    const std::vector<int>& mods = ext_set();
+    const int s_lo = S_req > 0 ? S_req : 1, s_hi = S_req > 0 ? S_req : 4096;
+    for (int S = s_lo; S <= s_hi; ++S) {
+        if ((double)Kpad * S * 127.0 * 127.0 >= ldexp(1.0, 31)) break;
+        const int w = (p + slack + S - 1) / S;
+        const double need = 2.0 * w + log2((double)K) + log2((double)S) + 5.0;
+        double cum = 0.0;
+        int N = 0;
+        for (int i = 0; i < (int)mods.size(); ++i) {
+            cum += log2((double)mods[i]);
+            if (cum > need) { N = i + 1; break; }
+        }
+        if (N == 0) continue;
+        Plan pl;
+        pl.p = p; pl.K = K; pl.Kpad = Kpad; pl.backend = OZLU_BE_INT8;
+        pl.S = S; pl.w = w; pl.Q = w * S; pl.N = N; pl.need = need;
+        pl.g0 = S - 1;
+        pl.G = S;
+        pl.pair_terms = 0;
+        for (int g = pl.g0; g <= 2 * S - 2; ++g) pl.pair_terms += std::min(g, 2 * S - 2 - g) + 1;
+        pl.ext = true;
+        pl.ext_mod.assign(mods.begin(), mods.begin() + N);
+        std::vector<uint32_t> P{1};
+        for (int i = 0; i < N; ++i) {
+            if (i < MAXMOD) pl.mod[i] = mods[i];
+            mul_small(P, (uint32_t)mods[i]);
+        }
+        pl.P = P;
+        pl.M.resize(N);
+        pl.ext_y.resize(N);
+        for (int i = 0; i < N; ++i) {
+            pl.M[i] = div_small(P, (uint32_t)mods[i]);
+            pl.ext_y[i] = inv_mod((int)mod_small(pl.M[i], (uint32_t)mods[i]), mods[i]);
+            if (i < MAXMOD) pl.y[i] = pl.ext_y[i];
+        }
+        pl.sbar_bits = 2 * w - 1 + ceil_log2((double)S * K) + 1;
+        pl.WG = (pl.sbar_bits + 31) / 32;
+        pl.pint_bits = w * (2 * S - 2 - pl.g0) + pl.sbar_bits;
+        pl.WX = 0;
+        pl.H = 0;
+        out = pl;
+        return OZLU_OK;
+    }
+    return OZLU_ERR_CAPACITY;
+}
+
+void build_ext_image(const Plan& pl, ExtImage& img) {
+    const int N = pl.N, WG = pl.WG;
+    const int WD = (pl.w + 2 + 31) / 32;  // words of one digit with its carry
+    img.WD = WD;
+    size_t off = 0;
+    auto take = [&](size_t words) {
+        const size_t o = off;
+        off += (words + 63) / 64 * 64;
+        return o;
+    };
+    img.o_mod = take(N);
+    img.o_y = take(N);
+    img.o_magic = take(N);
+    img.o_coef = take(3 * (size_t)N);
+    img.o_pw = take(N);
+    img.o_two32 = take(N);
+    img.o_inv40 = take(2 * (size_t)N);
+    img.o_pow32 = take((size_t)WD * N);
+    img.o_Mw = take((size_t)WG * N);
+    img.o_Pw = take(WG);
+    img.words.assign(off, 0u);
+    uint32_t* w = img.words.data();
+    for (int l = 0; l < N; ++l) {
+        const uint32_t m = (uint32_t)pl.ext_mod[l];
+        w[img.o_mod + l] = m;
+        w[img.o_y + l] = (uint32_t)pl.ext_y[l];
+        w[img.o_magic + l] = (uint32_t)(((1ull << 32) + m - 1) / m);
+        // C = P00 + 128 (Pss - P00 - P11) + 16384 P11 = (1 - 128) P00 + (16384 - 128) P11 + 128 Pss
+        w[img.o_coef + l] = (uint32_t)((m + (1 % m) - (128 % m)) % m);
+        w[img.o_coef + N + l] = (uint32_t)((16384 - 128) % m);
+        w[img.o_coef + 2 * N + l] = (uint32_t)(128 % m);
+        uint64_t r = 1 % m;
+        for (int k = 0; k < pl.w; ++k) r = (r * 2) % m;
+        w[img.o_pw + l] = (uint32_t)r;
+        w[img.o_two32 + l] = (uint32_t)((1ull << 32) % m);
+        const uint64_t inv = (uint64_t)(((unsigned __int128)1 << 40) / m +
+                                        ((((unsigned __int128)1 << 40) % m) * 2 >= m ? 1 : 0));
+        w[img.o_inv40 + 2 * l] = (uint32_t)inv;
+        w[img.o_inv40 + 2 * l + 1] = (uint32_t)(inv >> 32);
+        uint64_t pj = 1 % m;
+        for (int j = 0; j < WD; ++j) {
+            w[img.o_pow32 + (size_t)j * N + l] = (uint32_t)pj;
+            pj = (pj << 32) % m;
+        }
+        for (int j = 0; j < WG; ++j)
+            w[img.o_Mw + (size_t)j * N + l] = j < (int)pl.M[l].size() ? pl.M[l][j] : 0u;
+    }
+    for (int j = 0; j < WG; ++j) w[img.o_Pw + j] = j < (int)pl.P.size() ? pl.P[j] : 0u;
+}
+
 void fill_table(const Plan& pl, DevTable& t) {
     memset(&t, 0, sizeof t);
     t.N = pl.N; t.WG = pl.WG; t.H = pl.H; t.S = pl.S; t.w = pl.w; t.g0 = pl.g0;
@@ -248,5 +377,22 @@ extern "C" int ozlu_mp_plan(int p, int k, ozlu_plan_info* out) {
     out->Q = pl.Q; out->n_mod = pl.N; out->g0 = pl.g0; out->n_groups = pl.G;
     out->pair_terms = pl.pair_terms;
     for (int i = 0; i < pl.N && i < 64; ++i) out->moduli[i] = pl.mod[i];
+    return OZLU_OK;
+}
+
+extern "C" int ozlu_mp_plan_opts(int p, int k, const ozlu_opts* opts, ozlu_plan_info* out) {
+    if (p < 1) return -1;
+    if (k < 1) return -2;
+    if (!out) return -4;
+    const bool ext = opts && opts->modset == OZLU_MODSET_EXT;
+    if (opts && (opts->modset < 0 || opts->modset > OZLU_MODSET_EXT || opts->nslice < 0)) return -3;
+    ozlu::Plan pl;
+    const int rc = ext ? ozlu::make_plan_mp_ext(p, k, opts->nslice, pl) : ozlu::make_plan_mp(p, k, pl);
+    if (rc) return rc;
+    memset(out, 0, sizeof *out);
+    out->p = pl.p; out->K = pl.K; out->backend = pl.backend; out->S = pl.S; out->w = pl.w;
+    out->Q = pl.Q; out->n_mod = pl.N; out->g0 = pl.g0; out->n_groups = pl.G;
+    out->pair_terms = pl.pair_terms;
+    for (int i = 0; i < pl.N && i < 64; ++i) out->moduli[i] = ext ? pl.ext_mod[i] : pl.mod[i];
     return OZLU_OK;
 }

@@ -25,6 +25,8 @@ OZLU_ERR_NOMEM = 1002
 OZLU_ERR_CAPACITY = 1003
 OZLU_ERR_TIMEOUT = 1004
 OZLU_ERR_UNSUPPORTED = 1005
+OZLU_MODSET_INT8 = 0
+OZLU_MODSET_EXT = 1
 BACKENDS = {"auto": 0, "int8": 1, "fp8": 2, "fp64": 3, "fp16": 4}
 
 _lib = None
@@ -34,7 +36,8 @@ class ozlu_opts(ctypes.Structure):
     _fields_ = [("backend", ctypes.c_int), ("nslice", ctypes.c_int),
                 ("extra_groups", ctypes.c_int), ("g_ex", ctypes.c_int),
                 ("native", ctypes.c_int), ("graph", ctypes.c_int),
-                ("panel_width", ctypes.c_int), ("reserved", ctypes.c_int * 9)]
+                ("panel_width", ctypes.c_int), ("modset", ctypes.c_int),
+                ("reserved", ctypes.c_int * 8)]
 
 
 class ozlu_plan_info(ctypes.Structure):
@@ -51,7 +54,8 @@ class ozlu_stats(ctypes.Structure):
                 ("launches", ctypes.c_longlong), ("gemm_ops", ctypes.c_double),
                 ("crt_bytes", ctypes.c_double), ("convert_bytes", ctypes.c_double),
                 ("last_backend", ctypes.c_int), ("graph_status", ctypes.c_int),
-                ("trsm_ms", ctypes.c_double)]
+                ("trsm_ms", ctypes.c_double), ("last_nslice", ctypes.c_int),
+                ("tuned_nb", ctypes.c_int)]
 
 
 _P = ctypes.c_void_p
@@ -85,6 +89,8 @@ SIGNATURES = {
     "ozlu_mp_getrf": (_I, [_P, _I, _I, ctypes.POINTER(ozlu_mp_matrix), _P, _I, _P]),
     "ozlu_mp_getrs": (_I, [_P, _I, _I, _I, ctypes.POINTER(ozlu_mp_matrix), _P,
                            ctypes.POINTER(ozlu_mp_matrix)]),
+    "ozlu_mp_set_opts": (_I, [_P, ctypes.POINTER(ozlu_opts)]),
+    "ozlu_mp_plan_opts": (_I, [_I, _I, ctypes.POINTER(ozlu_opts), ctypes.POINTER(ozlu_plan_info)]),
     "ozlu_debug_fail_alloc": (_I, [_I]),
     "ozlu_debug_wait_expiry": (_I, [_P, _I, _L, _P]),
 }
@@ -116,11 +122,13 @@ def _check(fn, code):
         raise OzluError(fn, code)
 
 
-def make_opts(backend="int8", nslice=0, extra_groups=0, g_ex=0, native=0, graph=0, panel_width=0):
+def make_opts(backend="int8", nslice=0, extra_groups=0, g_ex=0, native=0, graph=0, panel_width=0,
+              modset=0):
     o = ozlu_opts()
     o.backend = BACKENDS[backend] if isinstance(backend, str) else int(backend)
     o.nslice, o.extra_groups, o.g_ex, o.native, o.graph = nslice, extra_groups, g_ex, native, graph
     o.panel_width = panel_width
+    o.modset = {"int8": OZLU_MODSET_INT8, "ext": OZLU_MODSET_EXT}.get(modset, modset)
     return o
 
 
@@ -169,6 +177,17 @@ def ozlu_mp_plan(p, k):
     info = ozlu_plan_info()
     _check("ozlu_mp_plan", lib().ozlu_mp_plan(p, k, ctypes.byref(info)))
     return info
+
+
+def ozlu_mp_plan_opts(p, k, opts=None):
+    info = ozlu_plan_info()
+    _check("ozlu_mp_plan_opts", lib().ozlu_mp_plan_opts(p, k, ctypes.byref(opts) if opts else None,
+                                                        ctypes.byref(info)))
+    return info
+
+
+def ozlu_mp_set_opts(h, opts=None):
+    _check("ozlu_mp_set_opts", lib().ozlu_mp_set_opts(h, ctypes.byref(opts) if opts else None))
 
 
 def ozlu_gemm(h, nc, p, m, n, k, alpha, A, lda, B, ldb, beta, C, ldc, opts=None):

@@ -118,12 +118,13 @@ static void run_conv(int n, uint64_t seed) {
 }
 
 // x mod m by one high multiply (mp_device.cuh mod_small, used for residues and
-// t values) against the % operator: every modulus m <= 255, x over edges and
-// a seeded sample of [0, 2^32)
+// t values) against the % operator: every modulus m <= 255 and every m of the
+// extended table's range up to 16191 (odd m from 257, the primes among them
+// included), x over edges and a seeded sample of [0, 2^32)
 static void run_mod() {
     std::mt19937_64 g(7);
     long long n = 0, bad = 0;
-    for (uint32_t m = 2; m <= 255; ++m) {
+    for (uint32_t m = 2; m <= 16191; m += (m < 255 ? 1 : 2)) {
         const uint32_t magic = (uint32_t)(((1ull << 32) + m - 1) / m);
         auto check = [&](uint32_t x) {
             ++n;
@@ -138,7 +139,7 @@ static void run_mod() {
             check((uint32_t)(mult - 1));
             check((uint32_t)(mult + 1));
         }
-        for (int i = 0; i < 20000; ++i) check((uint32_t)g());
+        for (int i = 0; i < (m <= 255 ? 20000 : 1500); ++i) check((uint32_t)g());
     }
     printf("mod %lld %lld\n", n, bad);
 }

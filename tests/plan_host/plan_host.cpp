@@ -14,6 +14,13 @@
 
 int main(int argc, char** argv) {
     using namespace ozlu;
+    if (argc > 1 && argv[1][0] == 'L') {
+        // Eq. (Lhint) seeds: arguments r t M N (quadruples after "L")
+        for (int i = 2; i + 3 < argc; i += 4)
+            printf("lhint %s %s %s %s %d\n", argv[i], argv[i + 1], argv[i + 2], argv[i + 3],
+                   lhint_S(atof(argv[i]), atoi(argv[i + 1]), atoi(argv[i + 2]), atoi(argv[i + 3])));
+        return 0;
+    }
     for (int i = 1; i + 2 < argc; i += 3) {
         const int p = atoi(argv[i]), K = atoi(argv[i + 1]), be = atoi(argv[i + 2]);
         Plan pl;

@@ -90,3 +90,26 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(ozlu, "_lib", None)
     with pytest.raises(RuntimeError):
         ozlu.lib()
+
+
+@pytest.mark.parametrize("p,k,S", [(64, 1, 0), (300, 9, 0), (600, 19, 2), (1100, 77, 0), (3136, 256, 0),
+                                   (6272, 256, 2), (12544, 256, 2), (12544, 1, 0), (11560, 512, 1)])
+def test_mp_ext_plan_matches_oracle(L, p, k, S):
+    # the extended-table planner of the p-bit GEMM (Sec. 4.2.4) against the
+    # oracle's rule: slice count, width, modulus count and the moduli
+    info = ozlu.ozlu_mp_plan_opts(p, k, ozlu.make_opts(modset="ext", nslice=S))
+    ref = make_plan(p, k, modset="ext", S=S or None)
+    assert (info.S, info.w, info.Q, info.n_mod, info.g0, info.pair_terms) == \
+        (ref.S, ref.w, ref.Q, ref.N, ref.g0, ref.pair_terms)
+    assert list(info.moduli)[:min(64, info.n_mod)] == list(ref.moduli)[:64]
+
+
+def test_mp_plan_opts_rejects_bad_options(L):
+    with pytest.raises(ozlu.OzluError):
+        ozlu.ozlu_mp_plan_opts(300, 9, ozlu.make_opts(modset=7))
+    with pytest.raises(ozlu.OzluError):
+        ozlu.ozlu_mp_plan_opts(11600, 512, ozlu.make_opts(modset="ext", nslice=1))   # beyond 23226 bits
+    # default options are the INT8 route
+    a = ozlu.ozlu_mp_plan_opts(3136, 256)
+    b = ozlu.ozlu_mp_plan(3136, 256)
+    assert (a.S, a.n_mod) == (b.S, b.n_mod)

@@ -88,7 +88,7 @@ def test_gemm_host_pointers_match_device():
     A, B = _pair(40, 30, 20, 4, 77)
     Ac, Bc = ozlu.to_colmajor(A), ozlu.to_colmajor(B)
     Cc = np.zeros((20, 40, 4))
-    ozlu.ozlu_gemm(h, 4, 0, 40, 20, 30, 1, Ac, 40, Bc, 30, 0, Cc, 40)
+    ozlu.ozlu_gemm(h, 4, 0, 40, 20, 30, 1, Ac, 40, Bc, 30, 0, Cc, 40, ozlu.make_opts("int8"))
     np.testing.assert_array_equal(ozlu.from_colmajor(Cc, 40), gpu_gemm(A, B))
 
 

@@ -221,3 +221,25 @@ def test_native_blocked_lu(nc, n, nb):
     assert bits < -53 * nc + math.log2(n) + 12, bits
     _, LU2, ipiv2, _ = _getrf(A, nb)
     np.testing.assert_array_equal(ipiv.cpu().numpy(), ipiv2)
+
+
+@pytest.mark.parametrize("nc,n", [(4, 70), (2, 45)])
+def test_native_unblocked_lu(nc, n):
+    # the unblocked naive comparison (b = 1, Sec. 3.4): same pivots as the
+    # oracle's p + 64-bit LU, exact backward error within the bound
+    h = handle()
+    A = random_expansions(n, n, nc, 1300 + n, -2, 2)
+    dA = dev(A)
+    ipiv = torch.zeros(n, dtype=torch.int32, device="cuda")
+    info = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ozlu.ozlu_getrf(h, nc, 0, n, dA, n, ipiv, 64, info, ozlu.make_opts("int8", native=2))
+    torch.cuda.synchronize()
+    LU = host(dA, n)
+    assert int(info.item()) == 0
+    piv = ipiv.cpu().numpy()
+    bits = _backward_error_bits(A, LU, piv)
+    assert bits < -53 * nc + math.log2(n) + 12, bits
+    prec = 53 * nc + 64
+    Af = [[_value(A[i, j]) for j in range(n)] for i in range(n)]
+    _, ipiv_ref, _ = olu.lu_bigfloat(olu.to_bigfloat_matrix(Af, prec), prec)
+    assert [p + 1 for p in ipiv_ref] == list(piv)

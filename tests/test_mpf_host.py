@@ -163,4 +163,4 @@ def test_to_expansion(cases):
 
 def test_mod_small(cases):
     (n, bad), = [v for o, L, v in cases if o == "mod"]
-    assert n > 5_000_000 and bad == 0
+    assert n > 40_000_000 and bad == 0

@@ -7,6 +7,7 @@ Eq. (11)): the moduli, y_l = (M_l mod m_l)^-1 mod m_l, the low 32-bit words
 of M_l = P / m_l and of P, 2^(16 j) mod m_l, ceil(2^32 / m_l) for the
 one-multiply reduction, and 1 / m_l rounded to binary32 for F.
 """
+import math
 import os
 import shutil
 import subprocess
@@ -96,3 +97,77 @@ def test_noalloc_table_equals_handle_planner(tables, p, K):
     assert na["N"] > 0
     ref = make_plan(p, K, backend="int8")
     assert (na["S"], na["w"], na["N"]) == (ref.S, ref.w, ref.N)
+
+
+EXT_CONFIGS = [(300, 9, 0), (600, 19, 2), (3136, 256, 0), (12544, 256, 2)]
+
+
+@pytest.fixture(scope="module")
+def ext_tables(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    inc = _cuda_include()
+    if cxx is None or inc is None:
+        pytest.skip("no C++ compiler or CUDA headers")
+    exe = str(tmp_path_factory.mktemp("ext") / "ext_host")
+    src = [os.path.join(ROOT, "tests", "plan_host", "ext_host.cpp"), SRC[1]]
+    subprocess.run([cxx, "-O1", "-std=c++17", "-I", INC, "-I", inc, "-o", exe, *src], check=True,
+                   capture_output=True, text=True)
+    args = [str(v) for c in EXT_CONFIGS for v in c]
+    out = subprocess.run([exe, *args], check=True, capture_output=True, text=True).stdout
+    res, cur = {}, None
+    for line in out.splitlines():
+        t = line.split()
+        if t[0] == "plan":
+            p, K, S, N, WG, WD, w = map(int, t[1:])
+            cur = {"N": N, "WG": WG, "WD": WD, "w": w, "mods": {}}
+            res[(p, K, S)] = cur
+        elif t[0] == "mod":
+            cur["mods"][int(t[1])] = [int(v) for v in t[2:]]
+        elif t[0] == "P":
+            cur["P"] = [int(v) for v in t[1:]]
+    return res
+
+
+@pytest.mark.parametrize("cfg", EXT_CONFIGS, ids=lambda c: f"p{c[0]}-K{c[1]}-S{c[2]}")
+def test_ext_tables_match_oracle(ext_tables, cfg):
+    # the device tables of the extended route (Sec. 4.2.4, Eq. (11)): moduli,
+    # y_l, ceil(2^32/m), the Karatsuba plane weights (1 - 128, 16384 - 128,
+    # 128) mod m, 2^w and 2^32 mod m, round(2^40/m), 2^(32 j) mod m, words of
+    # M_l and of P, recomputed from the oracle's plan
+    p, K, S = cfg
+    tab = ext_tables[cfg]
+    ref = make_plan(p, K, modset="ext", S=S or None)
+    WG, WD, w = tab["WG"], tab["WD"], ref.w
+    assert (tab["N"], tab["w"]) == (ref.N, ref.w)
+    assert WD == (w + 2 + 31) // 32
+    assert WG == (2 * w - 1 + math.ceil(math.log2(ref.S * K) - 1e-12) + 1 + 31) // 32
+    for l, v in tab["mods"].items():
+        m = ref.moduli[l]
+        M = ref.M[l]
+        inv = (1 << 40) // m + (1 if 2 * ((1 << 40) % m) >= m else 0)
+        want = [m, ref.y[l], -(-(1 << 32) // m), (1 - 128) % m, (16384 - 128) % m, 128 % m,
+                pow(2, w, m), (1 << 32) % m, inv, 1 % m, pow(2, 32, m), pow(2, 64, m),
+                pow(2, 32 * (WD - 1), m), M & 0xffffffff, (M >> 32) & 0xffffffff,
+                (M >> (32 * (WG - 1))) & 0xffffffff]
+        assert v == want, l
+    P = ref.P
+    assert tab["P"] == [P & 0xffffffff, (P >> 32) & 0xffffffff, (P >> (32 * (WG - 1))) & 0xffffffff]
+
+
+def test_autotuner_seed_is_eq_lhint(tmp_path):
+    # the autotuner seeds its slice count with Eq. (Lhint); the library's
+    # function (compiled for the host) against the oracle's formula
+    from oracle.plan import lhint_S
+    cxx = shutil.which("g++") or shutil.which("c++")
+    inc = _cuda_include()
+    if cxx is None or inc is None:
+        pytest.skip("no C++ compiler or CUDA headers")
+    exe = str(tmp_path / "plan_host")
+    subprocess.run([cxx, "-O1", "-std=c++17", "-I", INC, "-I", inc, "-o", exe, *SRC], check=True,
+                   capture_output=True, text=True)
+    cases = [(30, 132, 512, 512), (17.9, 238, 512, 512), (30, 238, 3840, 3840), (30, 6297, 256, 256),
+             (17.9, 185, 512, 512), (30, 12569, 64, 1), (30, 16, 1, 1), (30, 3161, 1792, 1792)]
+    args = ["L"] + [str(v) for c in cases for v in c]
+    out = subprocess.run([exe, *args], check=True, capture_output=True, text=True).stdout.split("\n")
+    got = [int(l.split()[-1]) for l in out if l.startswith("lhint")]
+    assert got == [lhint_S(*c) for c in cases]
