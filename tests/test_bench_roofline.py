@@ -44,9 +44,30 @@ def test_roofline_entry(dom, kernel, bound, unit):
     if dom in ("crt", "convert"):
         assert r["peak"] == PEAKS["hbm_gbs"]
     if dom == "panel":
-        assert r["traffic"] == bench.PANEL_TRAFFIC[(4096, 4, 256, 0)]
+        # the capture's traffic only while the kernel source is the captured one
+        bytes_, digest = bench.PANEL_TRAFFIC[(4096, 4, 256, 0)]
+        want = bytes_ if digest == bench.panel_source_digest() else None
+        assert r["traffic"] == want
+        assert r["work"]["limb_products"] == bench.panel_products(4096, 256)
     else:
         assert r["traffic"] is None
+
+
+def test_panel_products_count():
+    # base blocks of the recursive panel: 128-column leaves; column kc of a leaf
+    # (c0, w) costs (n - c0 - kc - 1) (w - kc) limb products; brute force
+    assert bench.panel_leaves(0, 256) == [(0, 128), (128, 128)]
+    assert bench.panel_leaves(0, 100) == [(0, 100)]
+    n, nb = 300, 256
+    total = 0
+    for r0 in range(0, n, nb):
+        b = min(nb, n - r0)
+        leaves = [(r0, b)] if b <= 128 else [(r0, b // 2), (r0 + b // 2, b - b // 2)]
+        for c0, w in leaves:
+            for kc in range(w):
+                rows = n - c0 - kc - 1
+                total += rows * 1 + rows * (w - kc - 1)
+    assert bench.panel_products(n, nb) == total
 
 
 def test_panel_traffic_only_for_the_captured_workload():
