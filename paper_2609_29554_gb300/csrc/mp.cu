@@ -143,6 +143,115 @@ __global__ void __launch_bounds__(256) mp_convert_kernel(MPView X, int R, int Kc
     }
 }
 
+// (S2)+(S3), one warp per element: the element's limbs are staged in shared
+// memory once, lane t forms the raw bits of digit t (bits [t w, (t + 1) w) of
+// |X|, X = trunc(a 2^mu)) with the flags the balanced digits need, lane 0
+// resolves the carries from digit to digit in order (Eq. (2): a digit that
+// reaches 2^(w-1) wraps to D - 2^w, for negative X to 2^w - D, and carries
+// one into the next), and the lanes then take the (digit, modulus) pairs:
+// residue of the raw digit by 16-bit chunks, plus the carry, the wrap
+// applied to the residue, the sign, centered.  The same planes as
+// mp_convert_kernel, whose single thread per element runs the limb loads and
+// the S N residues in sequence; this form keeps narrow products (a few
+// elements) from being latency-bound.
+constexpr int CW = 8;  // warps per block of mp_convert_warp_kernel
+
+__device__ __forceinline__ uint32_t sm_bits32(const uint32_t* lm, int L, long long pos) {
+    if (pos >= 32LL * L || pos <= -32) return 0;
+    const long long q = pos >= 0 ? (pos >> 5) : -((-pos + 31) >> 5);
+    const int r = (int)(pos - 32 * q);
+    const uint32_t lo = (q >= 0 && q < L) ? lm[q] : 0u;
+    const uint32_t hi = (q + 1 >= 0 && q + 1 < L) ? lm[q + 1] : 0u;
+    return r ? (lo >> r) | (hi << (32 - r)) : lo;
+}
+
+template <int H>
+__global__ void __launch_bounds__(32 * CW) mp_convert_warp_kernel(MPView X, int R, int Kc, int is_b,
+                                                                  const int* __restrict__ shifts,
+                                                                  const __grid_constant__ DevTable tab, int Kpad,
+                                                                  int Rpad, int8_t* __restrict__ planes,
+                                                                  int per_warp) {
+    extern __shared__ uint32_t wsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long task = (long long)blockIdx.x * CW + warp;
+    if (task >= (long long)R * Kc) return;
+    const int r = is_b ? (int)(task / Kc) : (int)(task % R);
+    const int h = is_b ? (int)(task % Kc) : (int)(task / R);
+    const size_t plane = (size_t)Rpad * Kpad, off = (size_t)r * Kpad + h;
+    const int S = tab.S, w = tab.w, N = tab.N, L = X.L;
+    const long long x = is_b ? (long long)h + (long long)r * X.ld : (long long)r + (long long)h * X.ld;
+    if (mp_zero(X, x)) {
+        for (int q = lane; q < N * S; q += 32) planes[(size_t)q * plane + off] = 0;
+        return;
+    }
+    uint32_t* lm = wsm + (size_t)warp * per_warp;  // L limbs
+    uint32_t* dw = lm + L;                         // S digits x MPD words
+    uint32_t* fl = dw + S * MPD;                   // S flag words
+    for (int k = lane; k < L; k += 32) lm[k] = X.limbs[(long long)k * X.plane + x];
+    __syncwarp();
+    const bool neg = X.signs[x] != 0;
+    const long long sh = 32LL * L - X.exps[x] - shifts[r];
+    const int nw = (w + 31) >> 5;
+    for (int t = lane; t < S; t += 32) {
+        bool lowzero = true, lowones = true;
+        uint32_t top = 0;
+#pragma unroll
+        for (int k = 0; k < MPD; ++k) {
+            uint32_t v = k < nw ? sm_bits32(lm, L, (long long)t * w + 32 * k + sh) : 0u;
+            const int hib = w - 32 * k;
+            if (hib < 32) v = hib > 0 ? (v & ((1u << hib) - 1u)) : 0u;
+            dw[t * MPD + k] = v;
+            const int lim = w - 1 - 32 * k;
+            if (lim >= 32) {
+                lowzero &= v == 0;
+                lowones &= v == 0xffffffffu;
+            } else if (lim >= 0) {
+                const uint32_t msk = lim ? (1u << lim) - 1u : 0u;
+                lowzero &= (v & msk) == 0;
+                lowones &= (v & msk) == msk;
+                top = (v >> lim) & 1u;
+            }
+        }
+        fl[t] = top | (lowzero ? 2u : 0u) | (lowones ? 4u : 0u);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        uint32_t carry = 0;
+        for (int t = 0; t < S; ++t) {
+            const uint32_t f = fl[t];
+            const bool top = f & 1u, lz = (f >> 1) & 1u, lo = (f >> 2) & 1u;
+            bool wrap = false;
+            if (t < S - 1) {
+                const bool ge = top || (carry && lo);
+                const bool half = carry ? (!top && lo) : (top && lz);
+                wrap = neg ? (ge && !half) : ge;
+            }
+            const bool dneg = wrap ? !neg : neg;
+            fl[t] = (carry << 3) | (wrap ? 16u : 0u) | (dneg ? 32u : 0u);
+            carry = wrap ? 1u : 0u;
+        }
+    }
+    __syncwarp();
+    for (int q = lane; q < N * S; q += 32) {
+        const int t = q / N, l = q - t * N;
+        const uint32_t m = (uint32_t)tab.mod[l], mg = tab.magic[l];
+        uint32_t acc = 0;
+#pragma unroll
+        for (int j = 0; j < H; ++j) acc += ((dw[t * MPD + (j >> 1)] >> (16 * (j & 1))) & 0xffffu) * tab.pow16[l][j];
+        uint32_t v = mod_small(acc, m, mg);
+        const uint32_t f = fl[t];
+        v = mod_small(v + ((f >> 3) & 1u), m, mg);
+        if ((f >> 4) & 1u) {
+            const uint32_t pw = mod_small(tab.pow16[l][w >> 4] << (w & 15), m, mg);  // 2^w mod m
+            v = mod_small(pw + m - v, m, mg);
+        }
+        if (((f >> 5) & 1u) && v) v = m - v;
+        int c = (int)v;
+        if (c > (int)(m - 1) / 2) c -= (int)m;
+        planes[(size_t)(l * S + t) * plane + off] = (int8_t)c;
+    }
+}
+
 // (S2)+(S3) with the extended modulus table (Sec. 4.2.4).  A warp takes 32
 // consecutive positions h of one row r (A side: element (r, h); B side:
 // element (h, r)), one per lane, so that every plane byte the warp writes is
@@ -249,10 +358,11 @@ __global__ void mp_convert_ext_kernel(MPView X, int R, int Kc, int is_b, const i
 }
 
 // ---- (S5)/(S6): CRT, recombination, fused update, rounding to p bits ----
-struct Acc {  // NW-word integer of this thread in shared memory, word k at w[k * MPCT]
+struct Acc {  // NW-word integer in shared memory, word k at w[k * st]
     uint32_t* w;
     int NW;
-    __device__ __forceinline__ uint32_t& operator[](int k) const { return w[k * MPCT]; }
+    int st;
+    __device__ __forceinline__ uint32_t& operator[](int k) const { return w[k * st]; }
 };
 
 __device__ void acc_negate(const Acc& A) {
@@ -374,7 +484,7 @@ __global__ void __launch_bounds__(MPCT) mp_crt_kernel(const uint8_t* __restrict_
     const long long mn = (long long)m * nchunk;
     if (e >= mn) return;
     const int i = (int)(e % m), jj = (int)(e / m), j = j0 + jj;
-    const Acc A{accsm + threadIdx.x, NW};
+    const Acc A{accsm + threadIdx.x, NW, MPCT};
     constexpr int WIN = WG + 2;
     long long win[WIN];
 #pragma unroll
@@ -444,7 +554,7 @@ __global__ void __launch_bounds__(MPCT) mp_crt_ext_kernel(const uint16_t* __rest
     const long long mn = (long long)m * nchunk;
     if (e >= mn) return;
     const int i = (int)(e % m), jj = (int)(e / m), j = j0 + jj;
-    const Acc A{accsm + threadIdx.x, NW};
+    const Acc A{accsm + threadIdx.x, NW, MPCT};
     for (int k = 0; k < NW; ++k) A[k] = 0;
     const int N = E.N, WG = E.WG;
     for (int gi = 0; gi < E.G; ++gi) {
@@ -505,6 +615,82 @@ void zero_k_padding(int8_t* planes, long long count, int R, int Rpad, int Kc, in
     cudaMemset2DAsync(planes + Kc, Kpad, 0, Kpad - Kc, (size_t)count * Rpad, s);
 }
 
+// (S5)+(S6) for few outputs: one warp per output, the lanes forming the S_g of
+// different digit groups in parallel (the N WG word products of each),
+// then lane 0 adds them into the NW-word accumulator through the same short
+// window as mp_crt_kernel and finishes with mp_finish.
+constexpr int CWC = 4;  // warps per block of mp_crt_warp_kernel
+
+template <int WG>
+__global__ void __launch_bounds__(32 * CWC) mp_crt_warp_kernel(const uint8_t* __restrict__ T, int m, int nchunk,
+                                                               int j0, const int* __restrict__ mu,
+                                                               const int* __restrict__ nu,
+                                                               const __grid_constant__ DevTable tab, int NW,
+                                                               int alpha, int beta, MPView C, int p) {
+    extern __shared__ uint32_t cwsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long e = (long long)blockIdx.x * CWC + warp;
+    const long long mn = (long long)m * nchunk;
+    if (e >= mn) return;
+    const int i = (int)(e % m), jj = (int)(e / m), j = j0 + jj;
+    const int G = tab.G;
+    uint32_t* sg = cwsm + (size_t)warp * ((size_t)G * WG + NW);  // S_g words [gi][WG]
+    uint32_t* aw = sg + (size_t)G * WG;                          // the accumulator
+    for (int gi = lane; gi < G; gi += 32) {
+        uint64_t a[WG];
+#pragma unroll
+        for (int wd = 0; wd < WG; ++wd) a[wd] = 0;
+        float F = 0.0f;
+        const uint8_t* tp = T + (size_t)gi * tab.N * mn + e;
+        for (int l = 0; l < tab.N; ++l) {
+            const uint32_t t = tp[(size_t)l * mn];
+#pragma unroll
+            for (int wd = 0; wd < WG; ++wd) a[wd] += (uint64_t)t * tab.Mlow[l][wd];
+            F = fmaf((float)t, tab.invm[l], F);
+        }
+        const uint32_t R = (uint32_t)rintf(F);
+        long long cy = 0;
+#pragma unroll
+        for (int wd = 0; wd < WG; ++wd) {
+            const long long cur = (long long)a[wd] + cy - (long long)((uint64_t)R * tab.Plow[wd]);
+            sg[gi * WG + wd] = (uint32_t)cur;
+            cy = cur >> 32;
+        }
+    }
+    __syncwarp();
+    if (lane != 0) return;
+    const Acc A{aw, NW, 1};
+    constexpr int WIN = WG + 2;
+    long long win[WIN];
+#pragma unroll
+    for (int k = 0; k < WIN; ++k) win[k] = 0;
+    int base = 0;
+    long long carry = 0;
+    auto retire = [&]() {
+        const long long v = win[0] + carry;
+        if (base < NW) A[base] = (uint32_t)v;
+        carry = v >> 32;  // arithmetic
+#pragma unroll
+        for (int k = 0; k < WIN - 1; ++k) win[k] = win[k + 1];
+        win[WIN - 1] = 0;
+        ++base;
+    };
+    for (int gi = 0; gi < G; ++gi) {
+        const uint32_t* Sg = sg + gi * WG;
+        const long long pos = (long long)tab.w * gi;
+        const int q = (int)(pos >> 5), r = (int)(pos & 31);
+        while (base < q) retire();
+#pragma unroll
+        for (int k = 0; k < WG; ++k) {
+            const uint32_t lo = k ? Sg[k - 1] : 0u;
+            win[k] += (long long)(r ? (Sg[k] << r) | (lo >> (32 - r)) : Sg[k]);
+        }
+        win[WG] += r ? (long long)((int)Sg[WG - 1] >> (32 - r)) : ((Sg[WG - 1] >> 31) ? -1LL : 0LL);
+    }
+    while (base < NW) retire();
+    mp_finish(A, NW, (long long)tab.w * tab.g0 - mu[i] - nu[j], alpha, beta, C, (long long)i + (long long)j * C.ld, p);
+}
+
 template <int H>
 void convert_h(const MPView& X, int R, int Kc, int is_b, const int* shifts, const DevTable& tab, int Kpad, int Rpad,
                int8_t* planes, cudaStream_t s) {
@@ -512,6 +698,16 @@ void convert_h(const MPView& X, int R, int Kc, int is_b, const int* shifts, cons
     zero_k_padding(planes, (long long)tab.N * tab.S, R, Rpad, Kc, Kpad, s);
     const long long total = (long long)R * Kc;
     if (total == 0) return;
+    {
+        const int per_warp = X.L + tab.S * (MPD + 1) + 1;
+        const size_t smem = sizeof(uint32_t) * (size_t)per_warp * CW;
+        if (smem <= 200 * 1024) {
+            raise_smem_limit((const void*)mp_convert_warp_kernel<H>, (int)smem);
+            mp_convert_warp_kernel<H><<<(unsigned)((total + CW - 1) / CW), 32 * CW, smem, s>>>(
+                X, R, Kc, is_b, shifts, tab, Kpad, Rpad, planes, per_warp);
+            return;
+        }
+    }
     mp_convert_kernel<H><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, R, Kc, is_b, shifts, tab, Kpad, Rpad,
                                                                          planes);
 }
@@ -531,6 +727,14 @@ template <int WG>
 void crt_wg(const uint8_t* T, int m, int nchunk, int j0, const int* mu, const int* nu, const DevTable& tab, int NW,
             int alpha, int beta, const MPView& C, int p, cudaStream_t s) {
     const long long mn = (long long)m * nchunk;
+    // few outputs: a warp per output (the digit groups in parallel)
+    const size_t wsm = sizeof(uint32_t) * ((size_t)tab.G * WG + NW) * CWC;
+    if (mn < 16384 && wsm <= 200 * 1024) {
+        raise_smem_limit((const void*)mp_crt_warp_kernel<WG>, (int)wsm);
+        mp_crt_warp_kernel<WG><<<(unsigned)((mn + CWC - 1) / CWC), 32 * CWC, wsm, s>>>(T, m, nchunk, j0, mu, nu,
+                                                                                      tab, NW, alpha, beta, C, p);
+        return;
+    }
     const size_t smem = sizeof(uint32_t) * (size_t)NW * MPCT;
     cudaFuncSetAttribute(mp_crt_kernel<WG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     mp_crt_kernel<WG><<<(unsigned)((mn + MPCT - 1) / MPCT), MPCT, smem, s>>>(T, m, nchunk, j0, mu, nu, tab, NW,

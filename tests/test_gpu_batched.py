@@ -98,3 +98,54 @@ def test_single_instance_graph_replay():
             np.testing.assert_array_equal(x.cpu().numpy(), xb.cpu().numpy())
     finally:
         ozlu.ozlu_destroy(h)
+
+
+def test_batched_against_oracle():
+    # the batched LU (default back-end choice, library panel widths, CUDA
+    # graph replay) against the oracle: every instance's pivots equal those of
+    # the oracle's p + 64-bit LU and its exact backward error P A - L U is
+    # within the bound; each solution of A x = A 1 (b formed exactly) reaches
+    # the accuracy the condition allows
+    import math
+    from fractions import Fraction
+
+    from exact_lu import ExactLU, l_bounded
+    from oracle import lu as olu
+    from synth import exact_row_sums, prescribed_cond_expansions
+
+    nc = 3
+    sizes = [40, 72, 17, 96]
+    conds = [20.0, 30.0, 25.0, 35.0]
+    mats = [prescribed_cond_expansions(n, c, 500 + i, nc).numpy() for i, (n, c) in enumerate(zip(sizes, conds))]
+    h = ozlu.ozlu_create(None)
+    try:
+        opts = ozlu.make_opts("auto", graph=1)
+        d0 = [dev(A) for A in mats]
+        dA = [x.clone() for x in d0]
+        piv = [torch.zeros(n, dtype=torch.int32, device="cuda") for n in sizes]
+        info = torch.full((len(sizes),), -7, dtype=torch.int32, device="cuda")
+        for _ in range(3):                        # eager, capture, replay
+            for x, y in zip(dA, d0):
+                x.copy_(y)
+            ozlu.ozlu_getrf_batched(h, nc, 0, sizes, dA, sizes, piv, info, 0, opts)
+        rhs = [exact_row_sums(torch.from_numpy(A), nc).view(1, n, nc).contiguous().cuda()
+               for A, n in zip(mats, sizes)]
+        ozlu.ozlu_getrs_batched(h, nc, 0, sizes, 1, dA, sizes, piv, rhs, sizes, ozlu.make_opts("auto"))
+        torch.cuda.synchronize()
+        assert ozlu.ozlu_get_stats(h).graph_status == 2
+        assert info.cpu().tolist() == [0] * len(sizes)
+        prec = 53 * nc + 64
+        for i, (A, n, c) in enumerate(zip(mats, sizes, conds)):
+            LU = host(dA[i], n)
+            ip = piv[i].cpu().numpy()
+            assert l_bounded(LU)
+            assert ExactLU(A, LU, ip).probe_bits(i) < -53 * nc + math.log2(n) + 12
+            Af = [[sum((Fraction(float(v)) for v in A[r, j]), Fraction(0)) for j in range(n)] for r in range(n)]
+            _, piv_ref, _ = olu.lu_bigfloat(olu.to_bigfloat_matrix(Af, prec), prec)
+            assert [p + 1 for p in piv_ref] == list(ip), i
+            x = rhs[i].cpu().numpy()[0]
+            err = max(abs(sum((Fraction(float(v)) for v in x[r]), Fraction(0)) - 1) for r in range(n))
+            bits = math.log2(err.denominator) - math.log2(err.numerator) if err else 159.0
+            assert bits > 159 - c * math.log2(10) - 10, (i, bits)
+    finally:
+        ozlu.ozlu_destroy(h)
