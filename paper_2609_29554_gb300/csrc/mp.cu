@@ -252,6 +252,145 @@ __global__ void __launch_bounds__(32 * CW) mp_convert_warp_kernel(MPView X, int 
     }
 }
 
+// (S2)+(S3) in plane order: a block takes 32 consecutive positions f of the
+// planes (f = r Kp + h, the K padding included), its 8 warps each form the
+// residues of 4 of them as mp_convert_warp_kernel does (a padding position or
+// a zero element gives zeros) into a shared tile [plane][32], and the block
+// then writes every plane's 32 bytes at once, contiguous.  With Kp = K
+// (unpadded planes of a small-K product) consecutive rows are adjacent, so
+// narrow operands are written as densely as wide ones.
+constexpr int TW = 8;  // warps per block of mp_convert_tile_kernel
+
+template <int H>
+__global__ void __launch_bounds__(32 * TW) mp_convert_tile_kernel(MPView X, int R, int Kc, int is_b,
+                                                                  const int* __restrict__ shifts,
+                                                                  const __grid_constant__ DevTable tab, int Kp,
+                                                                  int Rpad, int8_t* __restrict__ planes,
+                                                                  int per_warp) {
+    extern __shared__ uint32_t tsm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int S = tab.S, w = tab.w, N = tab.N, L = X.L, NS = N * S;
+    int8_t* tile = reinterpret_cast<int8_t*>(tsm);                           // [NS][32]
+    uint32_t* lm = tsm + (NS * 32 + 3) / 4 + (size_t)warp * per_warp;       // L limbs
+    uint32_t* dw = lm + L;                                                   // S x MPD digit words
+    uint32_t* fl = dw + S * MPD;                                             // S flag words
+    const long long f0 = (long long)blockIdx.x * 32;
+    const long long total = (long long)R * Kp;
+    for (int e = warp; e < 32; e += TW) {
+        const long long f = f0 + e;
+        const int r = (int)(f / Kp), h = (int)(f - (long long)r * Kp);
+        const long long x = is_b ? (long long)h + (long long)r * X.ld : (long long)r + (long long)h * X.ld;
+        if (f >= total || h >= Kc || mp_zero(X, x)) {
+            for (int q = lane; q < NS; q += 32) tile[q * 32 + e] = 0;
+            continue;
+        }
+        for (int k = lane; k < L; k += 32) lm[k] = X.limbs[(long long)k * X.plane + x];
+        __syncwarp();
+        const bool neg = X.signs[x] != 0;
+        const long long sh = 32LL * L - X.exps[x] - shifts[r];
+        const int nw = (w + 31) >> 5;
+        for (int t = lane; t < S; t += 32) {
+            bool lowzero = true, lowones = true;
+            uint32_t top = 0;
+#pragma unroll
+            for (int k = 0; k < MPD; ++k) {
+                uint32_t v = k < nw ? sm_bits32(lm, L, (long long)t * w + 32 * k + sh) : 0u;
+                const int hib = w - 32 * k;
+                if (hib < 32) v = hib > 0 ? (v & ((1u << hib) - 1u)) : 0u;
+                dw[t * MPD + k] = v;
+                const int lim = w - 1 - 32 * k;
+                if (lim >= 32) {
+                    lowzero &= v == 0;
+                    lowones &= v == 0xffffffffu;
+                } else if (lim >= 0) {
+                    const uint32_t msk = lim ? (1u << lim) - 1u : 0u;
+                    lowzero &= (v & msk) == 0;
+                    lowones &= (v & msk) == msk;
+                    top = (v >> lim) & 1u;
+                }
+            }
+            fl[t] = top | (lowzero ? 2u : 0u) | (lowones ? 4u : 0u);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            uint32_t carry = 0;
+            for (int t = 0; t < S; ++t) {
+                const uint32_t fg = fl[t];
+                const bool top = fg & 1u, lz = (fg >> 1) & 1u, lo = (fg >> 2) & 1u;
+                bool wrap = false;
+                if (t < S - 1) {
+                    const bool ge = top || (carry && lo);
+                    const bool half = carry ? (!top && lo) : (top && lz);
+                    wrap = neg ? (ge && !half) : ge;
+                }
+                const bool dneg = wrap ? !neg : neg;
+                fl[t] = (carry << 3) | (wrap ? 16u : 0u) | (dneg ? 32u : 0u);
+                carry = wrap ? 1u : 0u;
+            }
+        }
+        __syncwarp();
+        for (int q = lane; q < NS; q += 32) {
+            const int l = q / S, t = q - l * S;  // plane q = l S + t
+            const uint32_t m = (uint32_t)tab.mod[l], mg = tab.magic[l];
+            uint32_t acc = 0;
+#pragma unroll
+            for (int j = 0; j < H; ++j) acc += ((dw[t * MPD + (j >> 1)] >> (16 * (j & 1))) & 0xffffu) * tab.pow16[l][j];
+            uint32_t v = mod_small(acc, m, mg);
+            const uint32_t fg = fl[t];
+            v = mod_small(v + ((fg >> 3) & 1u), m, mg);
+            if ((fg >> 4) & 1u) {
+                const uint32_t pw = mod_small(tab.pow16[l][w >> 4] << (w & 15), m, mg);  // 2^w mod m
+                v = mod_small(pw + m - v, m, mg);
+            }
+            if (((fg >> 5) & 1u) && v) v = m - v;
+            int c = (int)v;
+            if (c > (int)(m - 1) / 2) c -= (int)m;
+            tile[q * 32 + e] = (int8_t)c;
+        }
+        __syncwarp();
+    }
+    __syncthreads();
+    // plane q: positions f0 .. f0 + 31, rows of Rpad x Kp (rows beyond R are not written)
+    const size_t plane = (size_t)Rpad * Kp;
+    for (int idx = threadIdx.x; idx < NS * 32; idx += 32 * TW) {
+        const int q = idx >> 5, e = idx & 31;
+        const long long f = f0 + e;
+        if (f < total) planes[(size_t)q * plane + f] = tile[q * 32 + e];
+    }
+}
+
+// (S4)+(S5 t_l) for K <= KSMALL on unpadded planes (Kp = K): one thread per
+// (i, j, l, g), the pair terms and K summed in int32 on the integer pipe.
+constexpr int KSMALL = 8;
+
+__global__ void __launch_bounds__(256) small_k_gemm_kernel(const int8_t* __restrict__ RA,
+                                                           const int8_t* __restrict__ RB, int m, int n, int K,
+                                                           const __grid_constant__ DevTable tab,
+                                                           uint8_t* __restrict__ T) {
+    const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    const long long mn = (long long)m * n;
+    if (idx >= mn * tab.N * tab.G) return;
+    const int i = (int)(idx % m);
+    long long rest = idx / m;
+    const int j = (int)(rest % n);
+    rest /= n;
+    const int l = (int)(rest % tab.N), gi = (int)(rest / tab.N);
+    const int S = tab.S, g = tab.g0 + gi;
+    const int ta0 = max(0, g - (S - 1)), ta1 = min(g, S - 1);
+    int acc = 0;
+    for (int ta = ta0; ta <= ta1; ++ta) {
+        const int tb = g - ta;
+        const int8_t* a = RA + (size_t)(l * S + ta) * m * K + (size_t)i * K;
+        const int8_t* b = RB + (size_t)(l * S + tb) * n * K + (size_t)j * K;
+        for (int h = 0; h < K; ++h) acc += (int)a[h] * (int)b[h];
+    }
+    const uint32_t md = (uint32_t)tab.mod[l], mg = tab.magic[l];
+    const uint32_t aa = acc < 0 ? (uint32_t)(-(long long)acc) : (uint32_t)acc;
+    uint32_t rr = mod_small(aa, md, mg);
+    if (acc < 0 && rr) rr = md - rr;
+    T[((size_t)gi * tab.N + l) * (size_t)mn + (size_t)j * m + i] = (uint8_t)mod_small(rr * (uint32_t)tab.y[l], md, mg);
+}
+
 // (S2)+(S3) with the extended modulus table (Sec. 4.2.4).  A warp takes 32
 // consecutive positions h of one row r (A side: element (r, h); B side:
 // element (h, r)), one per lane, so that every plane byte the warp writes is
@@ -695,19 +834,21 @@ template <int H>
 void convert_h(const MPView& X, int R, int Kc, int is_b, const int* shifts, const DevTable& tab, int Kpad, int Rpad,
                int8_t* planes, cudaStream_t s) {
     // rows [0, R) only (padded rows reach discarded outputs); zeros in the K padding
-    zero_k_padding(planes, (long long)tab.N * tab.S, R, Rpad, Kc, Kpad, s);
     const long long total = (long long)R * Kc;
     if (total == 0) return;
     {
+        // plane-ordered tiles: the K padding is written (zeros) by the kernel
         const int per_warp = X.L + tab.S * (MPD + 1) + 1;
-        const size_t smem = sizeof(uint32_t) * (size_t)per_warp * CW;
-        if (smem <= 200 * 1024) {
-            raise_smem_limit((const void*)mp_convert_warp_kernel<H>, (int)smem);
-            mp_convert_warp_kernel<H><<<(unsigned)((total + CW - 1) / CW), 32 * CW, smem, s>>>(
+        const size_t smem = sizeof(uint32_t) * ((size_t)(tab.N * tab.S * 32 + 3) / 4 + (size_t)per_warp * TW);
+        if (smem <= 220 * 1024) {
+            raise_smem_limit((const void*)mp_convert_tile_kernel<H>, (int)smem);
+            const long long positions = (long long)R * Kpad;
+            mp_convert_tile_kernel<H><<<(unsigned)((positions + 31) / 32), 32 * TW, smem, s>>>(
                 X, R, Kc, is_b, shifts, tab, Kpad, Rpad, planes, per_warp);
             return;
         }
     }
+    zero_k_padding(planes, (long long)tab.N * tab.S, R, Rpad, Kc, Kpad, s);
     mp_convert_kernel<H><<<(unsigned)((total + 255) / 256), 256, 0, s>>>(X, R, Kc, is_b, shifts, tab, Kpad, Rpad,
                                                                          planes);
 }
@@ -899,13 +1040,15 @@ int mp_gemm_device(ozlu_handle* h, int p, int m, int n, int k, int alpha, const 
     int rc = mp_plan_for(h, p, k, &pl, &tab);
     if (rc) return rc;
     cudaStream_t s = h->stream;
-    // residue planes padded in K to a multiple of the GEMM's K step (64),
-    // not of the plan's 128, so that narrow products stay narrow
-    const int Kpad = (k + 63) / 64 * 64, Mpad = (m + 127) / 128 * 128;
+    // K <= KSMALL: unpadded planes and the small-K product on the integer
+    // pipe; otherwise residue planes padded in K to a multiple of the GEMM's
+    // K step (64), not of the plan's 128, so that narrow products stay narrow
+    const bool smallk = k <= KSMALL;
+    const int Kpad = smallk ? k : (k + 63) / 64 * 64, Mpad = smallk ? m : (m + 127) / 128 * 128;
     const size_t planesN = (size_t)pl->N * pl->S;
     // n <= 16: 128 x 16 tiles and B planes of 16 rows
     const bool narrow = n <= 16;
-    const int rowq = narrow ? 16 : 128;
+    const int rowq = smallk ? 1 : (narrow ? 16 : 128);
     // column chunk: t values of one chunk below 4 GiB and B planes below 2 GiB
     const size_t tcol = (size_t)pl->G * pl->N * m;
     long long nch = (long long)(((size_t)4 << 30) / (tcol ? tcol : 1));
@@ -942,10 +1085,14 @@ int mp_gemm_device(ozlu_handle* h, int p, int m, int n, int k, int alpha, const 
         h->phase(PH_CONVERT);
         mp_convert(view_of(B, j0 * B.ld), nc, k, 1, nu + j0, *tab, Kpad, ncp, RB, s);
         h->phase(PH_GEMM);
-        if (narrow)
+        if (smallk) {
+            const long long work = (long long)m * nc * pl->N * pl->G;
+            small_k_gemm_kernel<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(RA, RB, m, nc, k, *tab, T);
+        } else if (narrow) {
             launch_gemm_imma_narrow(RA, RB, m, nc, Mpad, ncp, Kpad, *tab, T, s);
-        else
+        } else {
             launch_gemm_imma(RA, RB, m, nc, Mpad, ncp, Kpad, *tab, T, s);
+        }
         h->phase(PH_CRT);
         mp_crt(T, m, nc, (int)j0, mu, nu, *tab, NW, alpha, beta, vC, p, s);
         h->count(3);
