@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ozlu", choices=["ozlu", "reference"])
     ap.add_argument("--workload", default="lu", choices=["lu", "batched", "pbit"])
-    ap.add_argument("--n", type=int, default=None, help="lu 4096, pbit 512")
+    ap.add_argument("--n", type=int, default=None, help="lu 4096, pbit 1024")
     ap.add_argument("--nb", type=int, default=None, help="panel width (lu 256, batched 0 = library)")
     ap.add_argument("--nc", type=int, default=None, help="components (lu 4 = QD, batched 3 = TD)")
     ap.add_argument("--log10cond", type=float, default=40.0)
@@ -70,7 +70,7 @@ def parse():
                          "native blocked-naive expansion LU on the same matrix)")
     ap.add_argument("--no-pbit", action="store_true",
                     help="lu workload: skip the p-bit Lotkin sub-record")
-    ap.add_argument("--pbit-n", type=int, default=512,
+    ap.add_argument("--pbit-n", type=int, default=1024,
                     help="order of the p-bit Lotkin sub-record of the lu workload")
     ap.add_argument("--eager", action="store_true",
                     help="lu workload: launch every kernel directly instead of replaying a CUDA "
@@ -83,7 +83,7 @@ def parse():
                     help="oracle sample size (lu 352, batched 256)")
     a = ap.parse_args()
     lu = a.workload == "lu"
-    a.n = (512 if a.workload == "pbit" else 4096) if a.n is None else a.n
+    a.n = (1024 if a.workload == "pbit" else 4096) if a.n is None else a.n
     a.nb = (256 if lu else 0) if a.nb is None else a.nb
     a.nc = (4 if lu else 3) if a.nc is None else a.nc
     a.seed = (4 if lu else 5) if a.seed is None else a.seed

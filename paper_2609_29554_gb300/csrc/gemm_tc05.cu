@@ -19,9 +19,10 @@
 //   warp 1: one thread issues tcgen05.mma (M = 128, N = 128, K = 32 bytes
 //           per instruction) into TMEM, tcgen05.commit frees smem stages and
 //           hands a finished accumulator to the epilogue
-//   warps 2-9: epilogue (two warps per TMEM lane quarter, each on half of
-//           the columns), tcgen05.ld 32x32b, combine, t_l = (C mod m) y mod m,
-//           then free the accumulator buffer for the MMA warp
+//   warps 2-9 (FP8) or 2-17 (FP16): epilogue (two or four warps per TMEM
+//           lane quarter, each on a half or a quarter of the columns),
+//           tcgen05.ld 32x32b, combine, t_l = (C mod m) y mod m, then free the
+//           accumulator buffer for the MMA warp
 // Every mbarrier wait has an iteration limit; on expiry the CTA records
 // OZLU_ERR_TIMEOUT, stops issuing work, and releases its TMEM.
 #include <cuda.h>
@@ -35,8 +36,14 @@ namespace {
 
 constexpr int BM = 128, BN = 128, BK = 128;  // BK in bytes: one 128-byte swizzle row
 constexpr int STAGES = 6;
-constexpr int THREADS = 320;  // producer, MMA, 8 epilogue warps
-constexpr int EPI = THREADS - 64;  // epilogue threads
+// producer, MMA and the epilogue warps: 8 for FP8 (three accumulators per
+// output keep the registers of one epilogue thread high), 16 for FP16
+template <bool FP8>
+struct Cfg {
+    static constexpr int THREADS = FP8 ? 320 : 576;
+    static constexpr int EPI = THREADS - 64;      // epilogue threads
+    static constexpr int SPLIT = (THREADS - 64) / 128;  // column parts per TMEM lane quarter
+};
 constexpr int TILE = BM * BK;                // 16 KiB per operand stage
 constexpr long long WAIT_LIMIT = 1ll << 24;  // iterations of ~100 ns
 
@@ -137,7 +144,7 @@ __device__ __forceinline__ uint32_t t_value(int c, uint32_t m, uint32_t y, uint3
 // one 384-column buffer), so the epilogue of one tile overlaps the MMAs of
 // the next.
 template <bool FP8>
-__global__ void __launch_bounds__(THREADS, 1) gemm_tc05_kernel(
+__global__ void __launch_bounds__(Cfg<FP8>::THREADS, 1) gemm_tc05_kernel(
     const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int m, int n,
     int Mpad, int Npad, int KB, const __grid_constant__ DevTable tab, uint8_t* __restrict__ T,
     int* __restrict__ err) {
@@ -180,7 +187,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc05_kernel(
         }
         for (int b = 0; b < NBUF; ++b) {
             mbar_init(&accf[b], 1);
-            mbar_init(&acce[b], EPI);
+            mbar_init(&acce[b], Cfg<FP8>::EPI);
         }
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -263,10 +270,11 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc05_kernel(
             }
         }
     } else {
-        // epilogue warps 2..9: TMEM lane quarter = warp % 4; warps 2-5 take the
-        // first half of the tile's columns, warps 6-9 the second
+        // epilogue warps: TMEM lane quarter = warp % 4; the k-th group of four
+        // warps (from warp 2) takes the k-th of SPLIT parts of the tile's columns
         const int q = warp & 3;
         const int half = (warp - 2) >> 2;
+        constexpr int CPP = (BN / 32) / Cfg<FP8>::SPLIT;  // 32-column chunks per part
         int j = 0;
         for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++j) {
             int tm, tn, l, gi, ta0, items;
@@ -279,7 +287,7 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc05_kernel(
             const int i = tm * BM + q * 32 + lane;
             uint8_t* out = T + ((size_t)gi * tab.N + l) * (size_t)m * n;
             const uint32_t lane_addr = tmem + (uint32_t)(b * P * BN) + ((uint32_t)(q * 32) << 16);
-            for (int ch = half * (BN / 64); ch < (half + 1) * (BN / 64); ++ch) {
+            for (int ch = half * CPP; ch < (half + 1) * CPP; ++ch) {
                 uint32_t r0[32];
                 tmem_ld32(lane_addr + ch * 32, r0);
                 int c[32];
@@ -383,10 +391,10 @@ int launch_gemm_tc05(bool fp8, const void* RA, const void* RB, int m, int n, int
     dim3 grid((unsigned)(tiles < sms ? tiles : sms));
     if (fp8) {
         raise_smem_limit((const void*)gemm_tc05_kernel<true>, (int)smem);
-        gemm_tc05_kernel<true><<<grid, THREADS, smem, s>>>(ta, tb, m, n, Mpad, Npad, KB, tab, T, err);
+        gemm_tc05_kernel<true><<<grid, Cfg<true>::THREADS, smem, s>>>(ta, tb, m, n, Mpad, Npad, KB, tab, T, err);
     } else {
         raise_smem_limit((const void*)gemm_tc05_kernel<false>, (int)smem);
-        gemm_tc05_kernel<false><<<grid, THREADS, smem, s>>>(ta, tb, m, n, Mpad, Npad, KB, tab, T, err);
+        gemm_tc05_kernel<false><<<grid, Cfg<false>::THREADS, smem, s>>>(ta, tb, m, n, Mpad, Npad, KB, tab, T, err);
     }
     return cudaGetLastError() == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
 }
