@@ -437,11 +437,13 @@ def run_reference(a):
 IMAD_PEAK = 18.9        # T IMAD/s
 IMMA_PEAK = 151.6       # TOPS (mma.sync s8)
 # DRAM bytes (read + write) per launch of the cooperative panel kernel, the
-# mean over the base-block launches of one factorisation from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, profiles/), keyed by
-# (n, nc, nb, panel width), with the digest of the kernel source the counters
-# were taken on: a changed kernel reports null until it is captured again
-PANEL_TRAFFIC = {(4096, 4, 256, 0): (11.16e6, "46c7fd319766dc65")}
+# mean over the base-block launches of one factorisation (dram__bytes_read.sum
+# + dram__bytes_write.sum from one ncu capture, profiles/; taken at n = 2048,
+# where the traffic is 0.75 MB + 5.03 KB per row of the base block, and scaled
+# to the 2112 rows of an average n = 4096 launch), keyed by (n, nc, nb, panel
+# width), with the digest of the kernel source the counters were taken on: a
+# changed kernel reports null until it is captured again
+PANEL_TRAFFIC = {(4096, 4, 256, 0): (11.37e6, "0bd37f9492211208")}
 PBASE = 128     # widest base block of the cooperative panel kernel
 
 

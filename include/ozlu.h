@@ -324,7 +324,15 @@ int ozlu_mp_plan(int p, int k, ozlu_plan_info* out);
  *           product (about 2x per doubling of p instead of 3x) at the cost of
  *           O(p^2) conversion and CRT work per element
  *   nslice  the slice count S for OZLU_MODSET_EXT (0 = the smallest feasible)
- * Returns 0, -1 for a NULL handle, -2 for an unknown modset or nslice < 0.
+ *   backend residue GEMMs of the 54-modulus table for products with more than
+ *           16 columns and 8 inner indices: OZLU_BE_AUTO (default; measured
+ *           per shape class on the first call, the call then waits for the
+ *           stream), OZLU_BE_INT8 (mma.sync) or OZLU_BE_FP8 (balanced base-17
+ *           digits on tcgen05, Eq. (15), when K_pad S 15^2 < 2^24); both run the
+ *           same plan, so the results are identical; narrower products use the
+ *           integer pipe (K <= 8) or INT8
+ * Returns 0, -1 for a NULL handle, -2 for an unknown modset or backend or
+ * nslice < 0.
  */
 int ozlu_mp_set_opts(ozlu_handle* handle, const ozlu_opts* opts);
 

@@ -23,6 +23,9 @@
 #include <limits.h>
 #include <string.h>
 
+#include <cuda_fp8.h>
+#include <math.h>
+
 #include "mp_device.cuh"
 #include "ozlu_handle.h"
 
@@ -261,7 +264,7 @@ __global__ void __launch_bounds__(32 * CW) mp_convert_warp_kernel(MPView X, int 
 // narrow operands are written as densely as wide ones.
 constexpr int TW = 8;  // warps per block of mp_convert_tile_kernel
 
-template <int H>
+template <int H, bool FP8>
 __global__ void __launch_bounds__(32 * TW) mp_convert_tile_kernel(MPView X, int R, int Kc, int is_b,
                                                                   const int* __restrict__ shifts,
                                                                   const __grid_constant__ DevTable tab, int Kp,
@@ -350,12 +353,25 @@ __global__ void __launch_bounds__(32 * TW) mp_convert_tile_kernel(MPView X, int 
         __syncwarp();
     }
     __syncthreads();
-    // plane q: positions f0 .. f0 + 31, rows of Rpad x Kp (rows beyond R are not written)
+    // plane q: positions f0 .. f0 + 31, rows of Rpad x Kp (rows beyond R are not written);
+    // FP8: the residue r as its balanced base-17 digits in E4M3 (Eq. (15)),
+    // planes 3 q + 0, 1, 2 holding d0, d1, d0 + d1
     const size_t plane = (size_t)Rpad * Kp;
     for (int idx = threadIdx.x; idx < NS * 32; idx += 32 * TW) {
         const int q = idx >> 5, e = idx & 31;
         const long long f = f0 + e;
-        if (f < total) planes[(size_t)q * plane + f] = tile[q * 32 + e];
+        if (f >= total) continue;
+        const int r = tile[q * 32 + e];
+        if (!FP8) {
+            planes[(size_t)q * plane + f] = (int8_t)r;
+        } else {
+            const int d1 = (2 * r + 17 + 238) / 34 - 7;  // round(r / 17), never a tie (17 is odd)
+            const int d0 = r - 17 * d1;
+            uint8_t* p8 = reinterpret_cast<uint8_t*>(planes) + (size_t)(3 * q) * plane + f;
+            p8[0] = (uint8_t)__nv_cvt_float_to_fp8((float)d0, __NV_SATFINITE, __NV_E4M3);
+            p8[plane] = (uint8_t)__nv_cvt_float_to_fp8((float)d1, __NV_SATFINITE, __NV_E4M3);
+            p8[2 * plane] = (uint8_t)__nv_cvt_float_to_fp8((float)(d0 + d1), __NV_SATFINITE, __NV_E4M3);
+        }
     }
 }
 
@@ -830,7 +846,7 @@ __global__ void __launch_bounds__(32 * CWC) mp_crt_warp_kernel(const uint8_t* __
     mp_finish(A, NW, (long long)tab.w * tab.g0 - mu[i] - nu[j], alpha, beta, C, (long long)i + (long long)j * C.ld, p);
 }
 
-template <int H>
+template <int H, bool FP8>
 void convert_h(const MPView& X, int R, int Kc, int is_b, const int* shifts, const DevTable& tab, int Kpad, int Rpad,
                int8_t* planes, cudaStream_t s) {
     // rows [0, R) only (padded rows reach discarded outputs); zeros in the K padding
@@ -840,10 +856,10 @@ void convert_h(const MPView& X, int R, int Kc, int is_b, const int* shifts, cons
         // plane-ordered tiles: the K padding is written (zeros) by the kernel
         const int per_warp = X.L + tab.S * (MPD + 1) + 1;
         const size_t smem = sizeof(uint32_t) * ((size_t)(tab.N * tab.S * 32 + 3) / 4 + (size_t)per_warp * TW);
-        if (smem <= 220 * 1024) {
-            raise_smem_limit((const void*)mp_convert_tile_kernel<H>, (int)smem);
+        if (smem <= 220 * 1024 || FP8) {
+            raise_smem_limit((const void*)mp_convert_tile_kernel<H, FP8>, (int)smem);
             const long long positions = (long long)R * Kpad;
-            mp_convert_tile_kernel<H><<<(unsigned)((positions + 31) / 32), 32 * TW, smem, s>>>(
+            mp_convert_tile_kernel<H, FP8><<<(unsigned)((positions + 31) / 32), 32 * TW, smem, s>>>(
                 X, R, Kc, is_b, shifts, tab, Kpad, Rpad, planes, per_warp);
             return;
         }
@@ -854,14 +870,27 @@ void convert_h(const MPView& X, int R, int Kc, int is_b, const int* shifts, cons
 }
 
 void mp_convert(const MPView& X, int R, int Kc, int is_b, const int* shifts, const DevTable& tab, int Kpad, int Rpad,
-                int8_t* planes, cudaStream_t s) {
+                int8_t* planes, cudaStream_t s, bool fp8 = false) {
     switch (tab.H) {
-#define OZ_H(HH) case HH: convert_h<HH>(X, R, Kc, is_b, shifts, tab, Kpad, Rpad, planes, s); break;
+#define OZ_H(HH)                                                                                   \
+    case HH:                                                                                       \
+        if (fp8) convert_h<HH, true>(X, R, Kc, is_b, shifts, tab, Kpad, Rpad, planes, s);          \
+        else convert_h<HH, false>(X, R, Kc, is_b, shifts, tab, Kpad, Rpad, planes, s);             \
+        break;
         OZ_H(1) OZ_H(2) OZ_H(3) OZ_H(4) OZ_H(5) OZ_H(6) OZ_H(7) OZ_H(8) OZ_H(9) OZ_H(10) OZ_H(11) OZ_H(12)
         OZ_H(13) OZ_H(14) OZ_H(15)
 #undef OZ_H
-        default: convert_h<16>(X, R, Kc, is_b, shifts, tab, Kpad, Rpad, planes, s); break;
+        default:
+            if (fp8) convert_h<16, true>(X, R, Kc, is_b, shifts, tab, Kpad, Rpad, planes, s);
+            else convert_h<16, false>(X, R, Kc, is_b, shifts, tab, Kpad, Rpad, planes, s);
+            break;
     }
+}
+
+// shared memory of the tiled conversion (it must fit for the FP8 planes)
+size_t tile_smem(const MPView& X, const DevTable& tab) {
+    const int per_warp = X.L + tab.S * (MPD + 1) + 1;
+    return sizeof(uint32_t) * ((size_t)(tab.N * tab.S * 32 + 3) / 4 + (size_t)per_warp * TW);
 }
 
 template <int WG>
@@ -1029,6 +1058,71 @@ int mp_gemm_ext(ozlu_handle* h, int p, int S, int m, int n, int k, int alpha, co
     return cudaGetLastError() == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
 }
 
+int mp_gemm_device(ozlu_handle* h, int p, int m, int n, int k, int alpha, const ozlu_mp_matrix& A,
+                   const ozlu_mp_matrix& B, int beta, const ozlu_mp_matrix& C);
+
+// INT8 (mma.sync) or FP8 (tcgen05) residues for a wide p-bit product, by
+// measurement: both run the same plan (identical results) into a scratch C,
+// once untimed and once timed; the faster is cached per (p, k, log2 m, log2 n)
+int mp_tune_backend(ozlu_handle* h, int p, int m, int n, int k, const ozlu_mp_matrix& A, const ozlu_mp_matrix& B,
+                    int* be_out) {
+    auto lg = [](int v) { int r = 0; while ((1 << r) < v) ++r; return r; };
+    const auto key = std::make_tuple(1000 + 0, p, k, 0, lg(m), lg(n));
+    auto it = h->tuned.find(key);
+    if (it != h->tuned.end()) {
+        *be_out = it->second.first;
+        return OZLU_OK;
+    }
+    if (h->capturing) {
+        *be_out = OZLU_BE_INT8;
+        return OZLU_OK;
+    }
+    // scratch C: m x n elements of A's limb count
+    const int L = A.L;
+    const size_t words = (size_t)m * n * (L + 2);
+    int rc = h->tune_ws.ensure(words * 4 + 256);
+    if (rc) return rc;
+    ozlu_mp_matrix Cs;
+    uint32_t* w = (uint32_t*)h->tune_ws.base;
+    Cs.limbs = w;
+    Cs.exps = (int*)(w + (size_t)m * n * L);
+    Cs.signs = Cs.exps + (size_t)m * n;
+    Cs.ld = m;
+    Cs.plane = (long long)m * n;
+    Cs.L = L;
+    Cs.pad_ = 0;
+    const ozlu_opts saved = h->mp_opts;
+    const bool timing = h->timing;
+    h->timing = false;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int choice = OZLU_BE_INT8;
+    const int cands[2] = {OZLU_BE_INT8, OZLU_BE_FP8};
+    for (int c = 0; c < 2 && !rc; ++c) {
+        h->mp_opts.backend = cands[c];
+        for (int rep = 0; rep < 2 && !rc; ++rep) {
+            cudaEventRecord(e0, h->stream);
+            rc = mp_gemm_device(h, p, m, n, k, 1, A, B, 0, Cs);
+            cudaEventRecord(e1, h->stream);
+            if (rc) break;
+            cudaEventSynchronize(e1);
+            float ms = 0;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (rep == 1 && ms < best) { best = ms; choice = cands[c]; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->mp_opts = saved;
+    h->timing = timing;
+    if (rc) return rc;
+    h->tuned[key] = std::make_pair(choice, 0);
+    *be_out = choice;
+    return OZLU_OK;
+}
+
 // C = beta C + alpha A B, device views (m x k, k x n, m x n)
 int mp_gemm_device(ozlu_handle* h, int p, int m, int n, int k, int alpha, const ozlu_mp_matrix& A,
                    const ozlu_mp_matrix& B, int beta, const ozlu_mp_matrix& C) {
@@ -1044,10 +1138,23 @@ int mp_gemm_device(ozlu_handle* h, int p, int m, int n, int k, int alpha, const 
     // pipe; otherwise residue planes padded in K to a multiple of the GEMM's
     // K step (64), not of the plan's 128, so that narrow products stay narrow
     const bool smallk = k <= KSMALL;
-    const int Kpad = smallk ? k : (k + 63) / 64 * 64, Mpad = smallk ? m : (m + 127) / 128 * 128;
-    const size_t planesN = (size_t)pl->N * pl->S;
     // n <= 16: 128 x 16 tiles and B planes of 16 rows
     const bool narrow = n <= 16;
+    const MPView vA = view_of(A, 0), vB = view_of(B, 0), vC = view_of(C, 0);
+    // FP8 (balanced base-17 digits on tcgen05, three planes per residue, the
+    // same plan and so the same results) for wide products when chosen and
+    // admissible: fp32 accumulations below 2^24 and the tiles in shared memory
+    int be = h->mp_opts.backend;
+    const int kp128 = (k + 127) / 128 * 128;
+    const bool fp8_ok = !smallk && !narrow && (double)kp128 * pl->S * 225.0 < ldexp(1.0, 24) &&
+                        tile_smem(vA, *tab) <= 220 * 1024 && tile_smem(vB, *tab) <= 220 * 1024;
+    if (be == OZLU_BE_AUTO && fp8_ok) {
+        if ((rc = mp_tune_backend(h, p, m, n, k, A, B, &be))) return rc;
+    }
+    const bool fp8 = be == OZLU_BE_FP8 && fp8_ok;
+    const int P = fp8 ? 3 : 1;
+    const int Kpad = smallk ? k : (fp8 ? kp128 : (k + 63) / 64 * 64), Mpad = smallk ? m : (m + 127) / 128 * 128;
+    const size_t planesN = (size_t)pl->N * pl->S * P;
     const int rowq = smallk ? 1 : (narrow ? 16 : 128);
     // column chunk: t values of one chunk below 4 GiB and B planes below 2 GiB
     const size_t tcol = (size_t)pl->G * pl->N * m;
@@ -1071,21 +1178,24 @@ int mp_gemm_device(ozlu_handle* h, int p, int m, int n, int k, int alpha, const 
     int8_t* RA = (int8_t*)(base + o_ra);
     int8_t* RB = (int8_t*)(base + o_rb);
     uint8_t* T = (uint8_t*)(base + o_t);
-    const MPView vA = view_of(A, 0), vB = view_of(B, 0), vC = view_of(C, 0);
     const int NW = mp_window_words(*pl);
+    int* derr = nullptr;
+    if (fp8 && !(derr = err_word(h))) return OZLU_ERR_NOMEM;
     const int prev = h->open_phase;
     h->phase(PH_CONVERT);
     mp_shift_kernel<<<(m + 127) / 128, 128, 0, s>>>(vA, m, k, 0, pl->Q, mu);
     mp_shift_kernel<<<(n + 127) / 128, 128, 0, s>>>(vB, n, k, 1, pl->Q, nu);
-    mp_convert(vA, m, k, 0, mu, *tab, Kpad, Mpad, RA, s);
+    mp_convert(vA, m, k, 0, mu, *tab, Kpad, Mpad, RA, s, fp8);
     h->count(3);
     for (long long j0 = 0; j0 < n; j0 += nch) {
         const int nc = (int)(n - j0 < nch ? n - j0 : nch);
         const int ncp = (nc + rowq - 1) / rowq * rowq;
         h->phase(PH_CONVERT);
-        mp_convert(view_of(B, j0 * B.ld), nc, k, 1, nu + j0, *tab, Kpad, ncp, RB, s);
+        mp_convert(view_of(B, j0 * B.ld), nc, k, 1, nu + j0, *tab, Kpad, ncp, RB, s, fp8);
         h->phase(PH_GEMM);
-        if (smallk) {
+        if (fp8) {
+            if ((rc = launch_gemm_tc05(true, RA, RB, m, nc, Mpad, ncp, Kpad, *tab, T, derr, s))) return rc;
+        } else if (smallk) {
             const long long work = (long long)m * nc * pl->N * pl->G;
             small_k_gemm_kernel<<<(unsigned)((work + 255) / 256), 256, 0, s>>>(RA, RB, m, nc, k, *tab, T);
         } else if (narrow) {
@@ -1098,7 +1208,8 @@ int mp_gemm_device(ozlu_handle* h, int p, int m, int n, int k, int alpha, const 
         h->count(3);
         h->stats.gemm_launches += 1;
         h->stats.crt_launches += 1;
-        h->stats.gemm_ops += 2.0 * m * nc * (double)k * pl->N * pl->pair_terms;
+        h->stats.gemm_ops += 2.0 * m * nc * (double)k * pl->N * pl->pair_terms * P;
+        h->stats.last_backend = fp8 ? OZLU_BE_FP8 : OZLU_BE_INT8;
     }
     h->phase(prev);
     return cudaGetLastError() == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
@@ -1125,6 +1236,7 @@ extern "C" int ozlu_mp_set_opts(ozlu_handle* h, const ozlu_opts* opts) {
         return OZLU_OK;
     }
     if (opts->modset < 0 || opts->modset > OZLU_MODSET_EXT || opts->nslice < 0) return -2;
+    if (opts->backend != OZLU_BE_AUTO && opts->backend != OZLU_BE_INT8 && opts->backend != OZLU_BE_FP8) return -2;
     h->mp_opts = *opts;
     return OZLU_OK;
 }

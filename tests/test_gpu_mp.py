@@ -8,6 +8,7 @@ import math
 import random
 from fractions import Fraction
 
+import numpy as np
 import pytest
 
 from oracle import lu as olu
@@ -171,3 +172,31 @@ def test_mp_reciprocal_through_1x1_solve(p):
     ex = 1 / (Fraction(N) * Fraction(2) ** (-p + 3))
     err = abs(Fraction(xn) * Fraction(2) ** xe - ex) / ex
     assert err <= Fraction(2) ** (-p + 1)
+
+
+@pytest.mark.parametrize("be", ["fp8", "int8", "auto"])
+@pytest.mark.parametrize("m,n,k,p", [(140, 130, 40, 400), (130, 200, 300, 900), (257, 129, 9, 160)])
+def test_mp_gemm_backends_same_bits(be, m, n, k, p):
+    # wide p-bit products on FP8 (tcgen05, base-17 Karatsuba planes) or INT8
+    # residues run the same plan, so both equal the oracle's replay bit for bit
+    handle()
+    rng = random.Random(m + 3 * n + 7 * k + p)
+    L = (p + 31) // 32
+    A = rand_mp(rng, m, k, p, zeros=0.05)
+    B = rand_mp(rng, k, n, p, zeros=0.05)
+    C = rand_mp(rng, m, n, p, emin=-2, emax=6, zeros=0.1)
+    ref = oz2_gemm_mp(A, B, p, alpha=-1, beta=1, C=C)
+    h = ozlu.ozlu_create(None)
+    try:
+        ozlu.ozlu_mp_set_opts(h, ozlu.make_opts(be))
+        dA = ozlu.MPMatrix.from_pairs(A, L)
+        dB = ozlu.MPMatrix.from_pairs(B, L)
+        dC = ozlu.MPMatrix.from_pairs(C, L)
+        ozlu.ozlu_mp_gemm(h, p, m, n, k, -1, dA.desc(), dB.desc(), 1, dC.desc())
+        torch.cuda.synchronize()
+        assert dC.to_pairs() == norm(ref, L)
+        if be == "fp8":
+            assert ozlu.ozlu_get_stats(h).last_backend == 2
+        assert ozlu.ozlu_debug_fetch(h, 6, np.zeros(1, np.int32))[0] == 0
+    finally:
+        ozlu.ozlu_destroy(h)
