@@ -474,6 +474,11 @@ __device__ __forceinline__ void warp_best_key(unsigned long long& k, int& idx, i
     }
 }
 
+// named barrier of warps 1 .. COOP_THREADS / 32 - 1 (warp 0 takes no part)
+__device__ __forceinline__ void bar_rest() {
+    asm volatile("bar.sync 1, %0;" ::"r"(COOP_THREADS - 32) : "memory");
+}
+
 template <int N>
 __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
     double* A, long long lda, int n, int c0, int b, int p0, int p1, int rows_per_block,
@@ -485,11 +490,11 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
     // rows padded to b + 1 entries: threads on consecutive rows of one column
     // then fall on different shared-memory banks
     const int bs = b + 1;
-    __shared__ MPF<L> prow[PBASE];  // the pivot row
-    __shared__ MPF<L> otmp[PBASE];  // old row c (for the owner of the pivot row)
+    __shared__ MPF<L> prow[2][PBASE];  // the pivot row, double-buffered by column parity
+    __shared__ MPF<L> otmp[PBASE];     // old row c (for the owner of the pivot row)
     __shared__ MPF<L> rec;         // 1 / pivot
     __shared__ MPF<L> cv;          // this block's next candidate
-    __shared__ int ci, s_piv, s_widx, s_fail;
+    __shared__ int ci, s_piv, s_fail;
     __shared__ int s_pivs[PBASE];
     const int g = blockIdx.x, G = gridDim.x, tid = threadIdx.x;
     const int r0 = c0 + g * rows_per_block;
@@ -566,11 +571,21 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
     __syncthreads();
     publish(0);
     if (tid == 0) publish_rec(0);
+    // warps that share a scheduler with warp 0 (warp ids 4, 8, ...) leave the
+    // priority rows to the others, so that the reciprocal on thread 0 issues
+    // alone there
+    constexpr int NPRIO_T = 32 * (T / 32 - (T / 32 + 3) / 4);
+    const int warp = tid >> 5;
+    // the update of the rows outside the priority pair by column bulk_kc is
+    // deferred to the next column's exchange (bulk_kc < 0: none pending)
+    int bulk_kc = -1, bulk_lo = 0, bulk_pa = -1, bulk_pb = -1;
     for (int kc = 0; kc < b; ++kc) {
         const int c = c0 + kc;
-        // warp 0: wait for every stamp A of column kc, reduce the keys to the
-        // pivot, then wait for the winner's stamp B (its reciprocal)
+        MPF<L>* pr = prow[kc & 1];
         if (tid < 32) {
+            // warp 0: wait for every stamp A of column kc, reduce the keys to
+            // the pivot, wait for the winner's stamp B (its reciprocal), then
+            // load the pivot row, its reciprocal and index and old row c
             constexpr int PER = (COOP_MAXG + 31) / 32;
             const unsigned want = (unsigned)((c + 1) & 0xfffff);
             unsigned long long key[PER];
@@ -591,19 +606,17 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
                 key[u] &= KEY_MASK;
             }
             bool fail = __any_sync(0xffffffffu, !ok);
-            int W = -1;
+            __syncwarp();
             if (!fail) {
                 __threadfence();  // the slots' contents are visible after their stamps
                 unsigned long long K = 0;
-                int dummy = 0;
+                int W = -1, dummy = 0;
 #pragma unroll
                 for (int u = 0; u < PER; ++u) {
                     const int q = tid + 32 * u;
                     if (q < G && key[u] > 0 && (W < 0 || key[u] > K)) { K = key[u]; W = q; }
                 }
-                int Wl = W;
-                warp_best_key(K, Wl, dummy);  // lowest slot among equal keys
-                W = Wl;
+                warp_best_key(K, W, dummy);  // lowest slot among equal keys
                 int same = 0;
 #pragma unroll
                 for (int u = 0; u < PER; ++u) same += (tid + 32 * u < G && key[u] == K) ? 1 : 0;
@@ -625,57 +638,69 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
                     W = vw;
                 }
                 if (W < 0) W = 0;  // W >= 0: the owner of row c has a candidate
-                if (tid == 0) {
-                    const unsigned long long sb =
-                        wait_stamp(&sc->part[kc & 1][W].stamp_rec, want, &sc->error);
-                    s_fail = sb == 0 ? 1 : 0;
-                    if (sb) __threadfence();
+                int sb_ok = 1;
+                if (tid == 0)
+                    sb_ok = wait_stamp(&sc->part[kc & 1][W].stamp_rec, want, &sc->error) != 0;
+                fail = __shfl_sync(0xffffffffu, sb_ok, 0) == 0;
+                __syncwarp();
+                if (!fail) {
+                    __threadfence();
+                    const CoopSlot<L>& ws = sc->part[kc & 1][W];
+                    const int piv = __ldcg(&ws.idx);
+#pragma unroll
+                    for (int q = 0; q < PBASE / 32; ++q) {
+                        const int k = tid + 32 * q;
+                        if (k < b) pr[k] = ld_cg<L>(&ws.row[k]);
+                    }
+                    if (piv != c && owner(piv) == g) {
+#pragma unroll
+                        for (int q = 0; q < PBASE / 32; ++q) {
+                            const int k = tid + 32 * q;
+                            if (k < b) otmp[k] = ld_cg<L>(&sc->orow[kc & 1][k]);
+                        }
+                    }
+                    if (tid == 0) {
+                        rec = ld_cg<L>(&ws.rec);
+                        s_piv = piv;
+                    }
                 }
-                fail = __shfl_sync(0xffffffffu, tid == 0 ? s_fail : 0, 0) != 0;
             }
-            if (tid == 0) {
-                s_widx = W < 0 ? 0 : W;
-                s_fail = fail ? 1 : 0;
+            if (tid == 0) s_fail = fail ? 1 : 0;
+        } else if (bulk_kc >= 0) {
+            // warps 1 ..: the deferred update of the other rows by column bulk_kc
+            const int kb = bulk_kc, rest = b - kb - 2;
+            const MPF<L>* pk = prow[kb & 1];
+            const int total = (nr - bulk_lo) * rest;
+            for (int p = tid - 32; p < total; p += T - 32) {
+                const int r = bulk_lo + p / rest, k = kb + 2 + (p - (p / rest) * rest);
+                if (r == bulk_pa || r == bulk_pb) continue;
+                a[r * bs + k] = mpf_fms<L>(a[r * bs + k], a[r * bs + kb], pk[k]);
             }
         }
         __syncthreads();
         if (s_fail) return;
-        const int widx = s_widx;
-        // the pivot row, its reciprocal and index, and old row c (for the
-        // owner of the pivot row), all from L2 at once
-        // (b <= PBASE < T / 2 - 1: one element per thread)
-        if (tid < b)
-            prow[tid] = ld_cg<L>(&sc->part[kc & 1][widx].row[tid]);
-        else if (tid < 2 * b)
-            otmp[tid - b] = ld_cg<L>(&sc->orow[kc & 1][tid - b]);
-        else if (tid == 2 * b)
-            rec = ld_cg<L>(&sc->part[kc & 1][widx].rec);
-        else if (tid == 2 * b + 1)
-            s_piv = __ldcg(&sc->part[kc & 1][widx].idx);
-        __syncthreads();
         const int piv = s_piv;
         if (tid == 0) s_pivs[kc] = piv;
-        const bool zero = mpf_zero<L>(prow[kc]);
+        const bool zero = mpf_zero<L>(pr[kc]);
         if (g == 0 && tid == 0) {
             ipiv[c] = piv + 1;
             if (zero && *info == 0) *info = c + 1;
         }
         if (!zero && piv != c) {
             if (owner(c) == g)
-                for (int k = tid; k < b; k += T) a[(c - r0) * bs + k] = prow[k];
+                for (int k = tid; k < b; k += T) a[(c - r0) * bs + k] = pr[k];
             if (owner(piv) == g)
                 for (int k = tid; k < b; k += T) a[(piv - r0) * bs + k] = otmp[k];
         }
         __syncthreads();
         const int lo = max(r0, c + 1) - r0;
-        const int rows = nr - lo;
         const int cols = b - kc - 1;
         if (!zero) {
             // multipliers, then the next column first (its candidate is needed next)
             for (int r = lo + tid; r < nr; r += T) {
                 const MPF<L> l = mpf_mul<L>(a[r * bs + kc], rec);
                 a[r * bs + kc] = l;
-                if (cols > 0) a[r * bs + kc + 1] = mpf_fms<L>(a[r * bs + kc + 1], l, prow[kc + 1]);
+                if (cols > 0) a[r * bs + kc + 1] = mpf_fms<L>(a[r * bs + kc + 1], l, pr[kc + 1]);
             }
         }
         __syncthreads();
@@ -683,34 +708,46 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
         // warp 0: the next candidate
         if (tid < 32) candidate(kc + 1, c + 1);
         __syncthreads();
-        // the rows the next step reads from this block first: the candidate
-        // and (from its owner) row c + 1, which the pivot will replace
+        // the rows the next step reads from this block: the candidate and (from
+        // its owner) row c + 1, which the pivot will replace
         const int pa = ci >= 0 ? ci - r0 : -1;
         const int pb = owner(c + 1) == g ? c + 1 - r0 : -1;
         const int rest = cols - 1;
-        if (!zero && rest > 0) {
-            const int nprio = (pa >= 0 ? 1 : 0) + (pb >= 0 && pb != pa ? 1 : 0);
-            for (int p = tid; p < nprio * rest; p += T) {
-                const int which = p / rest, k = kc + 2 + (p - which * rest);
-                const int r = (which == 0 && pa >= 0) ? pa : pb;
-                a[r * bs + k] = mpf_fms<L>(a[r * bs + k], a[r * bs + kc], prow[k]);
-            }
-        }
-        __syncthreads();
-        publish(kc + 1);
-        // thread 0 forms and publishes the reciprocal while the other warps
-        // update the remaining rows
         if (tid == 0) {
+            // the candidate's reciprocal and stamp B, beside the priority rows
             publish_rec(kc + 1);
-        } else if (tid >= 32 && !zero && rest > 0) {
-            const int total = rows * rest;
-            for (int p = tid - 32; p < total; p += T - 32) {
-                const int r = lo + p / rest, k = kc + 2 + (p - (p / rest) * rest);
-                if (r == pa || r == pb) continue;
-                a[r * bs + k] = mpf_fms<L>(a[r * bs + k], a[r * bs + kc], prow[k]);
+        } else if (tid >= 32) {
+            if (!zero && rest > 0 && (warp & 3) != 0) {
+                const int nprio = (pa >= 0 ? 1 : 0) + (pb >= 0 && pb != pa ? 1 : 0);
+                const int pt = (warp - 1 - (warp >> 2)) * 32 + (tid & 31);
+                for (int p = pt; p < nprio * rest; p += NPRIO_T) {
+                    const int which = p / rest, k = kc + 2 + (p - which * rest);
+                    const int r = (which == 0 && pa >= 0) ? pa : pb;
+                    a[r * bs + k] = mpf_fms<L>(a[r * bs + k], a[r * bs + kc], pr[k]);
+                }
+            }
+            bar_rest();
+            // publish the candidate row of column kc + 1 and, from its owner,
+            // row c + 1; then stamp A with the key
+            CoopSlot<L>& slot = sc->part[(kc + 1) & 1][g];
+            const int wi = ci;
+            if (wi >= 0)
+                for (int k = tid - 32; k < b; k += T - 32) slot.row[k] = a[(wi - r0) * bs + k];
+            if (pb >= 0)
+                for (int k = tid - 32; k < b; k += T - 32) sc->orow[(kc + 1) & 1][k] = a[pb * bs + k];
+            if (tid == 32) slot.idx = wi;
+            bar_rest();
+            if (tid == 32) {
+                __threadfence();
+                const unsigned long long key = wi >= 0 ? mpf_key<L>(cv) : 0ull;
+                *reinterpret_cast<volatile unsigned long long*>(&slot.stamp) =
+                    ((unsigned long long)((c + 2) & 0xfffff) << STAMP_SHIFT) | key;
             }
         }
-        __syncthreads();
+        bulk_kc = (!zero && rest > 0) ? kc : -1;
+        bulk_lo = lo;
+        bulk_pa = pa;
+        bulk_pb = pb;
     }
     for (int p = tid; p < nr * b; p += T) {
         const int r = p / b, k = p - r * b;
