@@ -492,7 +492,7 @@ def roofline(st, a, peaks, src, fms=None, steps=None):
     dom = max(phases, key=phases.get)
     be = {1: "int8", 2: "fp8", 3: "fp64", 4: "fp16"}.get(st.last_backend, "int8")
     n, nc = a.n, a.nc
-    L = {2: 4, 3: 6, 4: 8}[nc]
+    L = {2: 4, 3: 6, 4: 7}[nc]
     if dom == "gemm":
         achieved = st.gemm_ops / (st.gemm_ms * 1e-3) / 1e12
         peak = {"int8": IMMA_PEAK, "fp8": 2 * peaks["bf16_tflops"], "fp16": peaks["bf16_tflops"],

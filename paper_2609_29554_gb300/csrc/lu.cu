@@ -37,9 +37,9 @@ constexpr int LCT = 4;          // laswp: columns per block
 constexpr int LHASH = 2048;     // laswp: hash slots (>= 2 x affected rows)
 constexpr int LMAXB = 512;      // laswp: interchanges per call
 
-// limbs of the panel arithmetic: 32 L >= 53 nc + 22
+// limbs of the panel arithmetic: 32 L >= 53 nc + 12 (DD 4, TD 6, QD 7)
 template <int N>
-struct Limbs { static constexpr int L = N == 2 ? 4 : (N == 3 ? 6 : 8); };
+struct Limbs { static constexpr int L = N == 2 ? 4 : (N == 3 ? 6 : 7); };
 
 struct LuScratch {
     uint32_t rm[8];             // reciprocal of the current pivot (MPF words)
@@ -560,7 +560,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
     // thread 0: the reciprocal of the candidate of column kc, then stamp B
     auto publish_rec = [&](int kc) {
         CoopSlot<L>& slot = sc->part[kc & 1][g];
-        const MPF<L> r = (ci >= 0 && !mpf_zero<L>(cv)) ? mpf_recip<L>(cv) : mpf_make_zero<L>();
+        const MPF<L> r = (ci >= 0 && !mpf_zero<L>(cv)) ? mpf_recip<L, true>(cv) : mpf_make_zero<L>();
         slot.rec = r;
         __threadfence();
         *reinterpret_cast<volatile unsigned long long*>(&slot.stamp_rec) =
@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
             for (int p = tid - 32; p < total; p += T - 32) {
                 const int r = bulk_lo + p / rest, k = kb + 2 + (p - (p / rest) * rest);
                 if (r == bulk_pa || r == bulk_pb) continue;
-                a[r * bs + k] = mpf_fms<L>(a[r * bs + k], a[r * bs + kb], pk[k]);
+                mpf_fms_ool<L>(&a[r * bs + k], &a[r * bs + k], &a[r * bs + kb], &pk[k]);
             }
         }
         __syncthreads();
@@ -698,9 +698,8 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
         if (!zero) {
             // multipliers, then the next column first (its candidate is needed next)
             for (int r = lo + tid; r < nr; r += T) {
-                const MPF<L> l = mpf_mul<L>(a[r * bs + kc], rec);
-                a[r * bs + kc] = l;
-                if (cols > 0) a[r * bs + kc + 1] = mpf_fms<L>(a[r * bs + kc + 1], l, pr[kc + 1]);
+                mpf_mul_ool<L>(&a[r * bs + kc], &a[r * bs + kc], &rec);
+                if (cols > 0) mpf_fms_ool<L>(&a[r * bs + kc + 1], &a[r * bs + kc + 1], &a[r * bs + kc], &pr[kc + 1]);
             }
         }
         __syncthreads();
@@ -723,7 +722,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
                 for (int p = pt; p < nprio * rest; p += NPRIO_T) {
                     const int which = p / rest, k = kc + 2 + (p - which * rest);
                     const int r = (which == 0 && pa >= 0) ? pa : pb;
-                    a[r * bs + k] = mpf_fms<L>(a[r * bs + k], a[r * bs + kc], pr[k]);
+                    mpf_fms_ool<L>(&a[r * bs + k], &a[r * bs + k], &a[r * bs + kc], &pr[k]);
                 }
             }
             bar_rest();

@@ -461,6 +461,32 @@ __device__ __forceinline__ MPF<L> mpf_fms(const MPF<L>& c, const MPF<L>& a, cons
     return add_windows<L, W>(C, c.e, c.neg, mpf_zero<L>(c), P, ep, a.neg ^ b.neg ^ 1, false, sticky);
 }
 
+// Out-of-line copies of the fused multiply-subtract and the product.  A kernel
+// whose warps run several of them at once on different code paths (the LU
+// panel) then keeps one copy of each in the instruction cache instead of one
+// per call site; the operands travel by address.
+template <int L>
+__device__ __noinline__ void mpf_fms_ool(MPF<L>* out, const MPF<L>* c, const MPF<L>* a, const MPF<L>* b) {
+    *out = mpf_fms<L>(*c, *a, *b);
+}
+
+template <int L>
+__device__ __noinline__ void mpf_mul_ool(MPF<L>* out, const MPF<L>* a, const MPF<L>* b) {
+    *out = mpf_mul<L>(*a, *b);
+}
+
+// c - a b by the inline (OOL = false) or the out-of-line copy
+template <int L, bool OOL>
+__device__ __forceinline__ MPF<L> mpf_fms_sel(const MPF<L>& c, const MPF<L>& a, const MPF<L>& b) {
+    if constexpr (OOL) {
+        MPF<L> r;
+        mpf_fms_ool<L>(&r, &c, &a, &b);
+        return r;
+    } else {
+        return mpf_fms<L>(c, a, b);
+    }
+}
+
 template <int L>
 __device__ __forceinline__ MPF<L> mpf_from_double(double v) {
     return mpf_from_exp<L, 1>(&v);
@@ -551,8 +577,9 @@ __device__ __forceinline__ MPF<4> mpf_recip_seed(uint64_t T) {
 // L = 4; second order, about 120 bits, otherwise), then one L-word step:
 // second order (about 240 bits) for L <= 6, third order (about 360 bits) for
 // L <= 11; longer formats continue with second-order steps.  Everything runs
-// on the integer pipes apart from one binary32 reciprocal.
-template <int L>
+// on the integer pipes apart from one binary32 reciprocal.  OOL: the fused
+// multiply-subtracts through their out-of-line copies.
+template <int L, bool OOL = false>
 __device__ __forceinline__ MPF<L> mpf_recip(const MPF<L>& b) {
     static_assert(L >= 4, "a 4-word first step");
     MPF<4> r4 = mpf_recip_seed(((uint64_t)b.m[L - 1] << 32) | b.m[L - 2]);
@@ -562,21 +589,21 @@ __device__ __forceinline__ MPF<L> mpf_recip(const MPF<L>& b) {
     f4.e = 0;
     f4.neg = 0;
     {
-        MPF<4> t4 = mpf_fms<4>(mpf_one<4>(), f4, r4);
+        MPF<4> t4 = mpf_fms_sel<4, OOL>(mpf_one<4>(), f4, r4);
         if (L == 4) t4 = mpf_add<4>(t4, mpf_top_square<4>(t4));
-        r4 = mpf_fms<4>(r4, r4, mpf_neg<4>(t4));
+        r4 = mpf_fms_sel<4, OOL>(r4, r4, mpf_neg<4>(t4));
     }
     MPF<L> r = mpf_widen<L, 4>(r4);
     if (L > 4) {
         MPF<L> f = b;
         f.neg = 0;
         f.e = 0;
-        MPF<L> t = mpf_fms<L>(mpf_one<L>(), f, r);
+        MPF<L> t = mpf_fms_sel<L, OOL>(mpf_one<L>(), f, r);
         if (L > 6) t = mpf_add<L>(t, mpf_top_square<L>(t));
-        r = mpf_fms<L>(r, r, mpf_neg<L>(t));
+        r = mpf_fms_sel<L, OOL>(r, r, mpf_neg<L>(t));
         for (int prec = L > 6 ? 360 : 240; prec < 32 * L + 8; prec *= 2) {
-            t = mpf_fms<L>(mpf_one<L>(), f, r);
-            r = mpf_fms<L>(r, r, mpf_neg<L>(t));
+            t = mpf_fms_sel<L, OOL>(mpf_one<L>(), f, r);
+            r = mpf_fms_sel<L, OOL>(r, r, mpf_neg<L>(t));
         }
     }
     r.e -= b.e;

@@ -14,6 +14,7 @@
 
 #define __device__
 #define __forceinline__ inline
+#define __noinline__
 static inline int __clz(uint32_t x) { return x ? __builtin_clz(x) : 32; }
 static inline int __clzll(long long x) { return x ? __builtin_clzll((unsigned long long)x) : 64; }
 static inline long long __double_as_longlong(double d) { long long r; memcpy(&r, &d, 8); return r; }
@@ -148,9 +149,11 @@ int main(int argc, char** argv) {
     const int n = argc > 1 ? atoi(argv[1]) : 1000;
     run<4>(n, 1);
     run<6>(n, 2);
+    run<7>(n, 7);
     run<8>(n, 3);
     run_conv<4, 2>(n, 4);
     run_conv<6, 3>(n, 5);
+    run_conv<7, 4>(n, 8);
     run_conv<8, 4>(n, 6);
     run_mod();
     return 0;

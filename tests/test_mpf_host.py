@@ -2,7 +2,7 @@
 
 `tests/mpf_host/mpf_host.cpp` compiles the device header `csrc/mpf.cuh` as
 plain C++ (portable definitions of the few CUDA intrinsics it uses) and prints
-seeded cases for L = 4, 6, 8 words; every result is checked here with exact
+seeded cases for L = 4, 6, 7, 8 words; every result is checked here with exact
 rational arithmetic:
   * mpf_mul, mpf_add: the exact result rounded to L words, to nearest even;
   * mpf_fms (c - a b with one rounding): the same, including exact
