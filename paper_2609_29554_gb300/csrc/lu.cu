@@ -638,31 +638,41 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
                     W = vw;
                 }
                 if (W < 0) W = 0;  // W >= 0: the owner of row c has a candidate
-                int sb_ok = 1;
-                if (tid == 0)
-                    sb_ok = wait_stamp(&sc->part[kc & 1][W].stamp_rec, want, &sc->error) != 0;
-                fail = __shfl_sync(0xffffffffu, sb_ok, 0) == 0;
-                __syncwarp();
-                if (!fail) {
-                    __threadfence();
-                    const CoopSlot<L>& ws = sc->part[kc & 1][W];
-                    const int piv = __ldcg(&ws.idx);
+                // the pivot row (under stamp A) with all loads in flight before
+                // the first shared-memory store, then the reciprocal (stamp B)
+                const CoopSlot<L>& ws = sc->part[kc & 1][W];
+                const int piv = __ldcg(&ws.idx);
+                constexpr int PL = PBASE / 32;
+                MPF<L> v[PL];
 #pragma unroll
-                    for (int q = 0; q < PBASE / 32; ++q) {
+                for (int q = 0; q < PL; ++q) {
+                    const int k = tid + 32 * q;
+                    if (k < b) v[q] = ld_cg<L>(&ws.row[k]);
+                }
+#pragma unroll
+                for (int q = 0; q < PL; ++q) {
+                    const int k = tid + 32 * q;
+                    if (k < b) pr[k] = v[q];
+                }
+                if (piv != c && owner(piv) == g) {
+#pragma unroll
+                    for (int q = 0; q < PL; ++q) {
                         const int k = tid + 32 * q;
-                        if (k < b) pr[k] = ld_cg<L>(&ws.row[k]);
+                        if (k < b) v[q] = ld_cg<L>(&sc->orow[kc & 1][k]);
                     }
-                    if (piv != c && owner(piv) == g) {
 #pragma unroll
-                        for (int q = 0; q < PBASE / 32; ++q) {
-                            const int k = tid + 32 * q;
-                            if (k < b) otmp[k] = ld_cg<L>(&sc->orow[kc & 1][k]);
-                        }
+                    for (int q = 0; q < PL; ++q) {
+                        const int k = tid + 32 * q;
+                        if (k < b) otmp[k] = v[q];
                     }
-                    if (tid == 0) {
-                        rec = ld_cg<L>(&ws.rec);
-                        s_piv = piv;
-                    }
+                }
+                int sb_ok = 1;
+                if (tid == 0) sb_ok = wait_stamp(&ws.stamp_rec, want, &sc->error) != 0;
+                fail = __shfl_sync(0xffffffffu, sb_ok, 0) == 0;
+                if (!fail && tid == 0) {
+                    __threadfence();
+                    rec = ld_cg<L>(&ws.rec);
+                    s_piv = piv;
                 }
             }
             if (tid == 0) s_fail = fail ? 1 : 0;
