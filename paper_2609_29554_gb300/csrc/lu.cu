@@ -684,7 +684,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
             for (int p = tid - 32; p < total; p += T - 32) {
                 const int r = bulk_lo + p / rest, k = kb + 2 + (p - (p / rest) * rest);
                 if (r == bulk_pa || r == bulk_pb) continue;
-                mpf_fms_ool<L>(&a[r * bs + k], &a[r * bs + k], &a[r * bs + kb], &pk[k]);
+                a[r * bs + k] = mpf_fms_oolv<L>(a[r * bs + k], a[r * bs + kb], pk[k]);
             }
         }
         __syncthreads();
@@ -709,7 +709,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
             // multipliers, then the next column first (its candidate is needed next)
             for (int r = lo + tid; r < nr; r += T) {
                 mpf_mul_ool<L>(&a[r * bs + kc], &a[r * bs + kc], &rec);
-                if (cols > 0) mpf_fms_ool<L>(&a[r * bs + kc + 1], &a[r * bs + kc + 1], &a[r * bs + kc], &pr[kc + 1]);
+                if (cols > 0) a[r * bs + kc + 1] = mpf_fms_oolv<L>(a[r * bs + kc + 1], a[r * bs + kc], pr[kc + 1]);
             }
         }
         __syncthreads();
@@ -732,7 +732,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
                 for (int p = pt; p < nprio * rest; p += NPRIO_T) {
                     const int which = p / rest, k = kc + 2 + (p - which * rest);
                     const int r = (which == 0 && pa >= 0) ? pa : pb;
-                    mpf_fms_ool<L>(&a[r * bs + k], &a[r * bs + k], &a[r * bs + kc], &pr[k]);
+                    a[r * bs + k] = mpf_fms_oolv<L>(a[r * bs + k], a[r * bs + kc], pr[k]);
                 }
             }
             bar_rest();

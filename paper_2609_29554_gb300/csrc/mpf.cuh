@@ -464,10 +464,12 @@ __device__ __forceinline__ MPF<L> mpf_fms(const MPF<L>& c, const MPF<L>& a, cons
 // Out-of-line copies of the fused multiply-subtract and the product.  A kernel
 // whose warps run several of them at once on different code paths (the LU
 // panel) then keeps one copy of each in the instruction cache instead of one
-// per call site; the operands travel by address.
+// per call site.  The fused multiply-subtract takes its operands and returns
+// its result by value (in registers); the product works on operands in
+// memory (shared memory in the panel), by address.
 template <int L>
-__device__ __noinline__ void mpf_fms_ool(MPF<L>* out, const MPF<L>* c, const MPF<L>* a, const MPF<L>* b) {
-    *out = mpf_fms<L>(*c, *a, *b);
+__device__ __noinline__ MPF<L> mpf_fms_oolv(MPF<L> c, MPF<L> a, MPF<L> b) {
+    return mpf_fms<L>(c, a, b);
 }
 
 template <int L>
@@ -479,9 +481,7 @@ __device__ __noinline__ void mpf_mul_ool(MPF<L>* out, const MPF<L>* a, const MPF
 template <int L, bool OOL>
 __device__ __forceinline__ MPF<L> mpf_fms_sel(const MPF<L>& c, const MPF<L>& a, const MPF<L>& b) {
     if constexpr (OOL) {
-        MPF<L> r;
-        mpf_fms_ool<L>(&r, &c, &a, &b);
-        return r;
+        return mpf_fms_oolv<L>(c, a, b);
     } else {
         return mpf_fms<L>(c, a, b);
     }
