@@ -21,7 +21,8 @@ calls).  Metric: sum_i 2 n_i^3 / 3 / t.
 --workload pbit: LU with partial pivoting of the Lotkin matrix (Sec. 4.4)
 stored as p-bit multi-limb numbers, p = 64 ceil(1.2 * 5.1 n / 64) (the
 paper's rule with log2 cond ~ 5.1 n; p = 12544 at n = 2048), nb = 256,
-ozlu_mp_getrf with INT8 residues; reports the solution error of A x = A 1
+ozlu_mp_getrf with the 54-modulus table (INT8 or FP8 residue GEMMs, chosen by
+measurement per product shape); reports the solution error of A x = A 1
 and the split of the time into residue GEMMs, modular reduction + CRT and
 conversion.  Metric: (2 n^3 / 3) / t in p-bit Gflop/s.
 
@@ -238,7 +239,7 @@ def main_pbit(a, rank, world, local, ozlu, torch):
             "warmup": a.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "u32 limbs (p-bit)", "data": "synthetic",
             "config": {"workload": f"p-bit LU with partial pivoting of the Lotkin matrix, n = {n}, "
-                                   f"p = {p}, INT8 residues", "n": n, "p": p, "limbs": r["limbs"],
+                                   f"p = {p}, INT8/FP8 residues", "n": n, "p": p, "limbs": r["limbs"],
                        "nb": r["nb"], "l2": "matrix copied in each step"},
             "roofline": rf, "gpu_launches": int(st.launches), "clocks": r["clocks"],
             "accuracy": {"solution_correct_bits": r["bits"], "p_minus_log2cond_estimate": p - 5.1 * n,
@@ -255,7 +256,7 @@ def pbit_subrecord(a, ozlu, torch):
     r = pbit_lu(a.pbit_n, 256, 1, 1, ozlu, torch, clocks=False)
     n = r["n"]
     return {"workload": f"p-bit LU with partial pivoting of the Lotkin matrix, n = {n}, "
-                        f"p = {r['p']}, INT8 residues",
+                        f"p = {r['p']}, INT8/FP8 residues",
             "value": 2.0 * n ** 3 / 3.0 / (r["ms"] * 1e-3) / 1e9, "unit": "Gflop/s",
             "ms": r["ms"], "n": n, "p": r["p"], "solution_correct_bits": r["bits"],
             "p_minus_log2cond_estimate": r["p"] - 5.1 * n,
@@ -439,11 +440,11 @@ IMMA_PEAK = 151.6       # TOPS (mma.sync s8)
 # DRAM bytes (read + write) per launch of the cooperative panel kernel, the
 # mean over the base-block launches of one factorisation (dram__bytes_read.sum
 # + dram__bytes_write.sum from one ncu capture, profiles/; taken at n = 2048,
-# where the traffic is 0.75 MB + 5.03 KB per row of the base block, and scaled
+# where the traffic is 0.58 MB + 5.12 KB per row of the base block, and scaled
 # to the 2112 rows of an average n = 4096 launch), keyed by (n, nc, nb, panel
 # width), with the digest of the kernel source the counters were taken on: a
 # changed kernel reports null until it is captured again
-PANEL_TRAFFIC = {(4096, 4, 256, 0): (11.37e6, "0bd37f9492211208")}
+PANEL_TRAFFIC = {(4096, 4, 256, 0): (11.39e6, "cc7f06c47e4638ff")}
 PBASE = 128     # widest base block of the cooperative panel kernel
 
 
