@@ -1299,7 +1299,8 @@ int lu_scratch(ozlu_handle* h, LuScratch** out) {
         if (!dev_alloc(&h->lu_scratch, sizeof(LuScratch))) return OZLU_ERR_NOMEM;
     }
     if (!h->coop_scratch) {
-        h->coop_bytes = sizeof(CoopScratch<8>);
+        h->coop_bytes = std::max(std::max(sizeof(CoopScratch<Limbs<2>::L>), sizeof(CoopScratch<Limbs<3>::L>)),
+                                 sizeof(CoopScratch<Limbs<4>::L>));
         if (!dev_alloc(&h->coop_scratch, h->coop_bytes)) {
             h->coop_scratch = nullptr;
             return OZLU_ERR_NOMEM;
@@ -1311,10 +1312,12 @@ int lu_scratch(ozlu_handle* h, LuScratch** out) {
 
 // the error word and the slot stamps start at zero for every factorisation
 int coop_reset(ozlu_handle* h, int nc, cudaStream_t s) {
+    // the slot layout is that of the panel kernel's limb count for nc
+    constexpr int L2 = Limbs<2>::L, L3 = Limbs<3>::L, L4 = Limbs<4>::L;
     switch (nc) {
-        case 2: coop_reset_kernel<4><<<1, 2 * COOP_MAXG, 0, s>>>((CoopScratch<4>*)h->coop_scratch); break;
-        case 3: coop_reset_kernel<6><<<1, 2 * COOP_MAXG, 0, s>>>((CoopScratch<6>*)h->coop_scratch); break;
-        default: coop_reset_kernel<8><<<1, 2 * COOP_MAXG, 0, s>>>((CoopScratch<8>*)h->coop_scratch); break;
+        case 2: coop_reset_kernel<L2><<<1, 2 * COOP_MAXG, 0, s>>>((CoopScratch<L2>*)h->coop_scratch); break;
+        case 3: coop_reset_kernel<L3><<<1, 2 * COOP_MAXG, 0, s>>>((CoopScratch<L3>*)h->coop_scratch); break;
+        default: coop_reset_kernel<L4><<<1, 2 * COOP_MAXG, 0, s>>>((CoopScratch<L4>*)h->coop_scratch); break;
     }
     h->count(1);
     return cudaGetLastError() == cudaSuccess ? OZLU_OK : OZLU_ERR_CUDA;
