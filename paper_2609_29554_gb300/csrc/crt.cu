@@ -119,13 +119,14 @@ __device__ __forceinline__ void wide_add_component(const Wide& X, double x, int 
     if (!neg) {
         wide_add_u64(X, mant, s);
     } else {
-        // subtract: X - mant 2^s = X + ~(mant 2^s) + 1 over all words
+        // subtract: X - mant 2^s = X + ~(mant 2^s) + 1 over the words from q
+        // up (below word q, ~0 + 1 leaves every word and the carry of 1)
         const int q = s >> 5, r = s & 31;
         const uint32_t p0 = (uint32_t)(mant << r);
         const uint32_t p1 = r ? (uint32_t)(mant >> (32 - r)) : (uint32_t)(mant >> 32);
         const uint32_t p2 = r ? (uint32_t)(mant >> (64 - r)) : 0u;
         uint64_t c = 1;
-        for (int k = 0; k < WACC; ++k) {
+        for (int k = q; k < WACC; ++k) {
             const uint32_t a = k == q ? p0 : k == q + 1 ? p1 : k == q + 2 ? p2 : 0u;
             const uint64_t t = (uint64_t)X[k] + (uint32_t)~a + c;
             X[k] = (uint32_t)t;
