@@ -575,7 +575,7 @@ __device__ __forceinline__ MPF<4> mpf_recip_seed(uint64_t T) {
 // each formed as r + r t by one more fused multiply-subtract.  A 4-word step
 // on the top 128 bits of f goes first (third order, about 180 bits, for
 // L = 4; second order, about 120 bits, otherwise), then one L-word step:
-// second order (about 240 bits) for L <= 6, third order (about 360 bits) for
+// second order (about 240 bits) for L <= 7, third order (about 360 bits) for
 // L <= 11; longer formats continue with second-order steps.  Everything runs
 // on the integer pipes apart from one binary32 reciprocal.  OOL: the fused
 // multiply-subtracts through their out-of-line copies.
@@ -599,9 +599,9 @@ __device__ __forceinline__ MPF<L> mpf_recip(const MPF<L>& b) {
         f.neg = 0;
         f.e = 0;
         MPF<L> t = mpf_fms_sel<L, OOL>(mpf_one<L>(), f, r);
-        if (L > 6) t = mpf_add<L>(t, mpf_top_square<L>(t));
+        if (L > 7) t = mpf_add<L>(t, mpf_top_square<L>(t));
         r = mpf_fms_sel<L, OOL>(r, r, mpf_neg<L>(t));
-        for (int prec = L > 6 ? 360 : 240; prec < 32 * L + 8; prec *= 2) {
+        for (int prec = L > 7 ? 360 : 240; prec < 32 * L + 8; prec *= 2) {
             t = mpf_fms_sel<L, OOL>(mpf_one<L>(), f, r);
             r = mpf_fms_sel<L, OOL>(r, r, mpf_neg<L>(t));
         }
