@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(CT) crt_kernel(const TT* __restrict__ T, int m
     if (e >= mn) return;
     const int i = (int)(e % m), j = (int)(e / m);
     const Wide X{sx + threadIdx.x}, Sg{ss + threadIdx.x};
-    wide_clear(X, WACC);
+    if (tab.G == 0) wide_clear(X, WACC);
 
     for (int gi = 0; gi < tab.G; ++gi) {
         uint64_t acc[WG];
@@ -215,14 +215,22 @@ __global__ void __launch_bounds__(CT) crt_kernel(const TT* __restrict__ T, int m
             F = fmaf((float)t, tab.invm[l], F);
         }
         const uint32_t R = (uint32_t)rintf(F);
+        // the first group sits at bit 0 of the window: it is written there
+        // (sign-extended) instead of added to a cleared window
+        const Wide& D = gi == 0 ? X : Sg;
         long long carry = 0;
 #pragma unroll
         for (int w = 0; w < WG; ++w) {
             const long long cur = (long long)acc[w] + carry - (long long)((uint64_t)R * tab.Plow[w]);
-            Sg[w] = (uint32_t)cur;
+            D[w] = (uint32_t)cur;
             carry = cur >> 32;  // arithmetic shift (floor)
         }
-        wide_add_shifted(X, Sg, WG, tab.w * gi);
+        if (gi == 0) {
+            const uint32_t sext = (X[WG - 1] >> 31) ? 0xffffffffu : 0u;
+            for (int k = WG; k < WACC; ++k) X[k] = sext;
+        } else {
+            wide_add_shifted(X, Sg, WG, tab.w * gi);
+        }
     }
     // X = P_int (two's complement) on the grid 2^E0
     int E = tab.w * tab.g0 - mu[i] - nu[j];

@@ -389,8 +389,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
-__device__ __forceinline__ unsigned long long ld_volatile(const unsigned long long* p) {
-    return *reinterpret_cast<const volatile unsigned long long*>(p);
+// load with acquire semantics at GPU scope: this thread's later loads see
+// everything the writer of the value made visible before it
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// store with release semantics at GPU scope
+__device__ __forceinline__ void st_release(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
 // wait until the stamp word carries column `want`; returns it, or 0 on
@@ -401,7 +410,7 @@ __device__ __forceinline__ unsigned long long wait_stamp(const unsigned long lon
                                                          unsigned long long limit_ns = COOP_WAIT_NS) {
     const unsigned long long t0 = global_ns();
     for (int it = 1;; ++it) {
-        const unsigned long long v = ld_volatile(p);
+        const unsigned long long v = ld_acquire(p);
         if ((unsigned)(v >> STAMP_SHIFT) == want) return v;
         if ((it & 63) == 0) {
             if (*(volatile int*)err) return 0;
@@ -562,9 +571,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
         CoopSlot<L>& slot = sc->part[kc & 1][g];
         const MPF<L> r = (ci >= 0 && !mpf_zero<L>(cv)) ? mpf_recip<L, true>(cv) : mpf_make_zero<L>();
         slot.rec = r;
-        __threadfence();
-        *reinterpret_cast<volatile unsigned long long*>(&slot.stamp_rec) =
-            (unsigned long long)((c0 + kc + 1) & 0xfffff) << STAMP_SHIFT;
+        st_release(&slot.stamp_rec, (unsigned long long)((c0 + kc + 1) & 0xfffff) << STAMP_SHIFT);
     };
 
     if (tid < 32) candidate(0, c0);
@@ -594,7 +601,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
             for (int u = 0; u < PER; ++u) {
                 const int q = tid + 32 * u;
                 key[u] = 0;
-                if (q < G) key[u] = ld_volatile(&sc->part[kc & 1][q].stamp);
+                if (q < G) key[u] = ld_acquire(&sc->part[kc & 1][q].stamp);
             }
 #pragma unroll
             for (int u = 0; u < PER; ++u) {
@@ -608,7 +615,7 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
             bool fail = __any_sync(0xffffffffu, !ok);
             __syncwarp();
             if (!fail) {
-                __threadfence();  // the slots' contents are visible after their stamps
+                // the slots' contents are visible after their stamps (acquire loads)
                 unsigned long long K = 0;
                 int W = -1, dummy = 0;
 #pragma unroll
@@ -670,7 +677,6 @@ __global__ void __launch_bounds__(COOP_THREADS, 1) base_block_coop_kernel(
                 if (tid == 0) sb_ok = wait_stamp(&ws.stamp_rec, want, &sc->error) != 0;
                 fail = __shfl_sync(0xffffffffu, sb_ok, 0) == 0;
                 if (!fail && tid == 0) {
-                    __threadfence();
                     rec = ld_cg<L>(&ws.rec);
                     s_piv = piv;
                 }
