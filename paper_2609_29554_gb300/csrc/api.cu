@@ -292,10 +292,30 @@ int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, c
     uint8_t* T = (uint8_t*)(base + L.t);
     const int prev = h->open_phase;
     h->phase(PH_CONVERT);
+    // B's exponents and residues on the side stream, beside A's (disjoint
+    // workspace regions); the first, eager call creates the stream
+    if (!h->side && !h->capturing) {
+        if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->side_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->side_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (h->side) cudaStreamDestroy(h->side);
+            if (h->side_fork) cudaEventDestroy(h->side_fork);
+            h->side = nullptr;
+            h->side_fork = nullptr;
+            h->side_join = nullptr;
+        }
+    }
+    const bool fork = h->side && cudaEventRecord(h->side_fork, s) == cudaSuccess &&
+                      cudaStreamWaitEvent(h->side, h->side_fork, 0) == cudaSuccess;
+    cudaStream_t sb = fork ? h->side : s;
+    launch_col_shifts(B, ldb, nc, k, n, pl->Q, nu, sb);
+    launch_convert(B, ldb, nc, k, n, true, nu, *tab, Kpad, Npad, RB, mode, sb);
     launch_row_shifts(A, lda, nc, m, k, pl->Q, mu, s);
-    launch_col_shifts(B, ldb, nc, k, n, pl->Q, nu, s);
     launch_convert(A, lda, nc, m, k, false, mu, *tab, Kpad, Mpad, RA, mode, s);
-    launch_convert(B, ldb, nc, k, n, true, nu, *tab, Kpad, Npad, RB, mode, s);
+    if (fork && (cudaEventRecord(h->side_join, h->side) != cudaSuccess ||
+                 cudaStreamWaitEvent(s, h->side_join, 0) != cudaSuccess))
+        return OZLU_ERR_CUDA;
     h->phase(PH_GEMM);
     if (mode == 0) {
         launch_gemm_imma((const int8_t*)RA, (const int8_t*)RB, m, n, Mpad, Npad, Kpad, *tab, T, s);
@@ -404,6 +424,9 @@ int ozlu_destroy(ozlu_handle* h) {
     }
     if (h->fork) cudaEventDestroy(h->fork);
     if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->side_fork) cudaEventDestroy(h->side_fork);
+    if (h->side_join) cudaEventDestroy(h->side_join);
     if (h->dev_err) cudaFree(h->dev_err);
     for (auto& e : h->ext_plans)
         if (e.second.dev) cudaFree(e.second.dev);

@@ -45,6 +45,10 @@ struct ozlu_handle {
     std::map<std::tuple<int, int, int, int, int, int>, ozlu::PlanEntry> plans;
     ozlu::GemmLayout last;
     int* dev_err = nullptr;  // device error word of the tensor-core GEMMs
+    // second stream of the GEMM's conversion: B's exponents and residues run
+    // beside A's (fork / join events on the handle's stream)
+    cudaStream_t side = nullptr;
+    cudaEvent_t side_fork = nullptr, side_join = nullptr;
     bool timing = false;
     ozlu_stats stats = {};
     void* lu_scratch = nullptr;  // pivot-search scratch of ozlu_getrf
