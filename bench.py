@@ -440,11 +440,11 @@ IMMA_PEAK = 151.6       # TOPS (mma.sync s8)
 # DRAM bytes (read + write) per launch of the cooperative panel kernel, the
 # mean over the base-block launches of one factorisation (dram__bytes_read.sum
 # + dram__bytes_write.sum from one ncu capture, profiles/; taken at n = 2048,
-# where the traffic is 0.58 MB + 5.12 KB per row of the base block, and scaled
+# where the traffic is 0.56 MB + 5.12 KB per row of the base block, and scaled
 # to the 2112 rows of an average n = 4096 launch), keyed by (n, nc, nb, panel
 # width), with the digest of the kernel source the counters were taken on: a
 # changed kernel reports null until it is captured again
-PANEL_TRAFFIC = {(4096, 4, 256, 0): (11.39e6, "cc7f06c47e4638ff")}
+PANEL_TRAFFIC = {(4096, 4, 256, 0): (11.36e6, "bbd712b36bcf70cf")}
 PBASE = 128     # widest base block of the cooperative panel kernel
 
 
