@@ -239,6 +239,32 @@ int autotune(ozlu_handle* h, int nc, int p, int m, int n, int k, const double* A
 
 // The device part of one GEMM, all pointers on the device.
 
+cudaStream_t side_fork(ozlu_handle* h, cudaStream_t s) {
+    // the first call outside a capture creates the stream and its events
+    if (!h->side && !h->capturing) {
+        if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->side_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->side_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            if (h->side) cudaStreamDestroy(h->side);
+            if (h->side_fork) cudaEventDestroy(h->side_fork);
+            h->side = nullptr;
+            h->side_fork = nullptr;
+            h->side_join = nullptr;
+        }
+    }
+    if (h->side && cudaEventRecord(h->side_fork, s) == cudaSuccess &&
+        cudaStreamWaitEvent(h->side, h->side_fork, 0) == cudaSuccess)
+        return h->side;
+    cudaGetLastError();
+    return s;
+}
+
+bool side_join(ozlu_handle* h, cudaStream_t s, cudaStream_t side) {
+    if (side == s) return true;
+    return cudaEventRecord(h->side_join, side) == cudaSuccess && cudaStreamWaitEvent(s, h->side_join, 0) == cudaSuccess;
+}
+
 int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, const double* A,
                 long long lda, const double* B, long long ldb, int beta, double* C,
                 long long ldc, const ozlu_opts* opts) {
@@ -293,29 +319,13 @@ int gemm_device(ozlu_handle* h, int nc, int p, int m, int n, int k, int alpha, c
     const int prev = h->open_phase;
     h->phase(PH_CONVERT);
     // B's exponents and residues on the side stream, beside A's (disjoint
-    // workspace regions); the first, eager call creates the stream
-    if (!h->side && !h->capturing) {
-        if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&h->side_fork, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&h->side_join, cudaEventDisableTiming) != cudaSuccess) {
-            cudaGetLastError();
-            if (h->side) cudaStreamDestroy(h->side);
-            if (h->side_fork) cudaEventDestroy(h->side_fork);
-            h->side = nullptr;
-            h->side_fork = nullptr;
-            h->side_join = nullptr;
-        }
-    }
-    const bool fork = h->side && cudaEventRecord(h->side_fork, s) == cudaSuccess &&
-                      cudaStreamWaitEvent(h->side, h->side_fork, 0) == cudaSuccess;
-    cudaStream_t sb = fork ? h->side : s;
+    // workspace regions)
+    cudaStream_t sb = side_fork(h, s);
     launch_col_shifts(B, ldb, nc, k, n, pl->Q, nu, sb);
     launch_convert(B, ldb, nc, k, n, true, nu, *tab, Kpad, Npad, RB, mode, sb);
     launch_row_shifts(A, lda, nc, m, k, pl->Q, mu, s);
     launch_convert(A, lda, nc, m, k, false, mu, *tab, Kpad, Mpad, RA, mode, s);
-    if (fork && (cudaEventRecord(h->side_join, h->side) != cudaSuccess ||
-                 cudaStreamWaitEvent(s, h->side_join, 0) != cudaSuccess))
-        return OZLU_ERR_CUDA;
+    if (!side_join(h, s, sb)) return OZLU_ERR_CUDA;
     h->phase(PH_GEMM);
     if (mode == 0) {
         launch_gemm_imma((const int8_t*)RA, (const int8_t*)RB, m, n, Mpad, Npad, Kpad, *tab, T, s);

@@ -1183,15 +1183,22 @@ int mp_gemm_device(ozlu_handle* h, int p, int m, int n, int k, int alpha, const 
     if (fp8 && !(derr = err_word(h))) return OZLU_ERR_NOMEM;
     const int prev = h->open_phase;
     h->phase(PH_CONVERT);
-    mp_shift_kernel<<<(m + 127) / 128, 128, 0, s>>>(vA, m, k, 0, pl->Q, mu);
-    mp_shift_kernel<<<(n + 127) / 128, 128, 0, s>>>(vB, n, k, 1, pl->Q, nu);
-    mp_convert(vA, m, k, 0, mu, *tab, Kpad, Mpad, RA, s, fp8);
+    // B's exponents and first column chunk on the side stream, beside A's
+    {
+        cudaStream_t sb = side_fork(h, s);
+        const int nc0 = (int)(n < nch ? n : nch);
+        mp_shift_kernel<<<(n + 127) / 128, 128, 0, sb>>>(vB, n, k, 1, pl->Q, nu);
+        mp_convert(vB, nc0, k, 1, nu, *tab, Kpad, (nc0 + rowq - 1) / rowq * rowq, RB, sb, fp8);
+        mp_shift_kernel<<<(m + 127) / 128, 128, 0, s>>>(vA, m, k, 0, pl->Q, mu);
+        mp_convert(vA, m, k, 0, mu, *tab, Kpad, Mpad, RA, s, fp8);
+        if (!side_join(h, s, sb)) return OZLU_ERR_CUDA;
+    }
     h->count(3);
     for (long long j0 = 0; j0 < n; j0 += nch) {
         const int nc = (int)(n - j0 < nch ? n - j0 : nch);
         const int ncp = (nc + rowq - 1) / rowq * rowq;
         h->phase(PH_CONVERT);
-        mp_convert(view_of(B, j0 * B.ld), nc, k, 1, nu + j0, *tab, Kpad, ncp, RB, s, fp8);
+        if (j0 > 0) mp_convert(view_of(B, j0 * B.ld), nc, k, 1, nu + j0, *tab, Kpad, ncp, RB, s, fp8);
         h->phase(PH_GEMM);
         if (fp8) {
             if ((rc = launch_gemm_tc05(true, RA, RB, m, nc, Mpad, ncp, Kpad, *tab, T, derr, s))) return rc;

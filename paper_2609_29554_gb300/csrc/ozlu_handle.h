@@ -105,5 +105,11 @@ int* err_word(ozlu_handle* h);
 int mp_gemm_device(ozlu_handle* h, int p, int m, int n, int k, int alpha, const ozlu_mp_matrix& A,
                    const ozlu_mp_matrix& B, int beta, const ozlu_mp_matrix& C);
 int clear_err_word(ozlu_handle* h);
+// the handle's second stream, forked from s (made by the first call outside a
+// graph capture); s itself when there is none
+cudaStream_t side_fork(ozlu_handle* h, cudaStream_t s);
+// s waits for the work issued on `side` (nothing when side is s); false on a
+// CUDA error
+bool side_join(ozlu_handle* h, cudaStream_t s, cudaStream_t side);
 int cuda_rc(cudaError_t e);
 }  // namespace ozlu
