@@ -99,7 +99,10 @@ typedef struct {
 
 /* Create a handle bound to a CUDA stream (cudaStream_t passed as void*; NULL =
  * the default stream).  The current device at creation is the handle's
- * device.  Returns OZLU_ERR_CUDA when no device is usable. */
+ * device.  Calls may fork independent kernels onto a second stream the handle
+ * owns (made on the first call outside a graph capture) and join it back into
+ * the handle's stream before they return, so the work stays ordered on the
+ * handle's stream.  Returns OZLU_ERR_CUDA when no device is usable. */
 int ozlu_create(ozlu_handle** handle, void* stream);
 /* Release the workspace and the handle.  NULL is accepted. */
 int ozlu_destroy(ozlu_handle* handle);
