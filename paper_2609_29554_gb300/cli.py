@@ -1,6 +1,6 @@
 """Command-line runs of single library calls on seeded inputs.
 
-    python -m paper_2609_29554_gb300.cli gemm  --n 2048 --nc 4 --backend fp8
+    python -m paper_2609_29554_gb300.cli gemm  --n 2048 --nc 4 --backend fp8 [--schur]
     python -m paper_2609_29554_gb300.cli getrf --n 4096 --nc 4 --nb 256 [--matrix cond|random]
 
 Each run builds the library if needed, generates its input with synth/,
@@ -29,6 +29,8 @@ def main(argv=None):
     ap.add_argument("--backend", default="auto")
     ap.add_argument("--matrix", default="random", choices=["random", "cond"])
     ap.add_argument("--reps", type=int, default=1)
+    ap.add_argument("--schur", action="store_true",
+                    help="gemm as the LU's trailing update: C <- C - A B on a random C")
     a = ap.parse_args(argv)
     import torch
 
@@ -42,10 +44,16 @@ def main(argv=None):
         k = a.k or n
         A = torch.from_numpy(ozlu.to_colmajor(random_expansions(n, k, nc, 1))).cuda()
         B = torch.from_numpy(ozlu.to_colmajor(random_expansions(k, n, nc, 2))).cuda()
-        C = torch.zeros((n, n, nc), dtype=torch.float64, device="cuda")
+        if a.schur:
+            C0 = torch.from_numpy(ozlu.to_colmajor(random_expansions(n, n, nc, 3, -1, 1))).cuda()
+        else:
+            C0 = torch.zeros((n, n, nc), dtype=torch.float64, device="cuda")
+        C = torch.empty_like(C0)
+        alpha, beta = (-1, 1) if a.schur else (1, 0)
 
         def call():
-            ozlu.ozlu_gemm(h, nc, 0, n, n, k, 1, A, n, B, k, 0, C, n, opts)
+            C.copy_(C0)
+            ozlu.ozlu_gemm(h, nc, 0, n, n, k, alpha, A, n, B, k, beta, C, n, opts)
         flops = 2.0 * n * n * k
     else:
         if a.matrix == "cond":
