@@ -36,6 +36,7 @@ constexpr int STEP_ROWS = 16;   // rows per block of a column step
 constexpr int LCT = 4;          // laswp: columns per block
 constexpr int LHASH = 2048;     // laswp: hash slots (>= 2 x affected rows)
 constexpr int LMAXB = 512;      // laswp: interchanges per call
+constexpr int TRI_SLOTS = 8;    // triangles of base solves converted ahead (256 / BASE)
 
 // limbs of the panel arithmetic: 32 L >= 53 nc + 12 (DD 4, TD 6, QD 7)
 template <int N>
@@ -52,9 +53,10 @@ struct LuScratch {
     double pval[MAXPART][4];    // block candidates (expansion values)
     int pidx[MAXPART];
     int plist[1 + 4 * LMAXB];   // interchange permutation: count, (dst, src) pairs
-    // triangle of a base triangular solve as L-limb floats: [k][i], then the
-    // reciprocal diagonal (upper case)
-    unsigned char tri[(BASE * BASE + BASE) * sizeof(MPF<8>)];
+    // triangles of base triangular solves as L-limb floats: [k][i], then the
+    // reciprocal diagonal (upper case); slot q holds the q-th diagonal block of
+    // a unit lower triangle converted ahead of its recursion
+    unsigned char tri[TRI_SLOTS][(BASE * BASE + BASE) * sizeof(MPF<8>)];
 };
 
 template <int L>
@@ -925,12 +927,15 @@ __global__ void __launch_bounds__(256) naive_update_kernel(const double* A, long
 }
 
 // The b x b triangle of a base triangular solve, converted once to L-limb
-// floats (and the reciprocal diagonal for the upper case) in the scratch.
+// floats (and the reciprocal diagonal for the upper case) in the scratch:
+// blockIdx.y = q converts the q-th b x b diagonal block from T into slot q.
 template <int N>
 __global__ void __launch_bounds__(256) tri_convert_kernel(const double* T, long long ldt, int b, int lower,
                                                           LuScratch* sc) {
     constexpr int L = Limbs<N>::L;
-    MPF<L>* tl = reinterpret_cast<MPF<L>*>(sc->tri);
+    const int q = blockIdx.y;
+    T += ((long long)q * b + (long long)q * b * ldt) * N;
+    MPF<L>* tl = reinterpret_cast<MPF<L>*>(sc->tri[q]);
     MPF<L>* rd = tl + BASE * BASE;
     for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < b * b; idx += gridDim.x * blockDim.x) {
         const int i = idx / b, k = idx - i * b;
@@ -950,14 +955,14 @@ __global__ void __launch_bounds__(256) tri_convert_kernel(const double* T, long 
 // read from shared memory column by column ([k][i], conflict-free).
 template <int N>
 __global__ void __launch_bounds__(256) trsm_base_kernel(const LuScratch* sc, double* X, long long ldx, int b,
-                                                        int ncols, int lower) {
+                                                        int ncols, int lower, int slot) {
     constexpr int L = Limbs<N>::L;
     extern __shared__ __align__(16) unsigned char smraw[];
     MPF<L>* sl = reinterpret_cast<MPF<L>*>(smraw);   // [k][i]
     MPF<L>* rd = sl + BASE * BASE;                   // reciprocal diagonal (upper)
     const int row = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int col = blockIdx.x * (blockDim.x >> 5) + w;
-    const MPF<L>* tl = reinterpret_cast<const MPF<L>*>(sc->tri);
+    const MPF<L>* tl = reinterpret_cast<const MPF<L>*>(sc->tri[slot]);
     for (int idx = threadIdx.x; idx < BASE * BASE; idx += blockDim.x) sl[idx] = tl[idx];
     if (!lower)
         for (int k = threadIdx.x; k < b; k += blockDim.x) rd[k] = tl[BASE * BASE + k];
@@ -978,17 +983,21 @@ __global__ void __launch_bounds__(256) trsm_base_kernel(const LuScratch* sc, dou
     if (row < b) mpf_to_exp<L, N>(x, xp);
 }
 
+// slot < 0: convert the triangle into slot 0 first; else it is in `slot`
 template <int N>
 void trsm_base(const double* T, long long ldt, double* X, long long ldx, int b, int ncols, int lower,
-               LuScratch* sc, cudaStream_t s) {
+               LuScratch* sc, cudaStream_t s, int slot = -1) {
     if (ncols <= 0 || b <= 0) return;
     constexpr int L = Limbs<N>::L;
-    tri_convert_kernel<N><<<(b * b + 255) / 256, 256, 0, s>>>(T, ldt, b, lower, sc);
+    if (slot < 0) {
+        tri_convert_kernel<N><<<(b * b + 255) / 256, 256, 0, s>>>(T, ldt, b, lower, sc);
+        slot = 0;
+    }
     // 8 columns (warps) per block, fewer when that leaves SMs idle
     const int wpb = ncols >= 8 * 152 ? 8 : (ncols >= 4 * 152 ? 4 : 2);
     const size_t smem = sizeof(MPF<L>) * (BASE * BASE + BASE);
     raise_smem_limit((const void*)trsm_base_kernel<N>, (int)smem);
-    trsm_base_kernel<N><<<(ncols + wpb - 1) / wpb, 32 * wpb, smem, s>>>(sc, X, ldx, b, ncols, lower);
+    trsm_base_kernel<N><<<(ncols + wpb - 1) / wpb, 32 * wpb, smem, s>>>(sc, X, ldx, b, ncols, lower, slot);
 }
 
 // Launch the cooperative base-block kernel; returns false when the slice of
@@ -1058,21 +1067,33 @@ int coop_width(const Ctx& c, int) {
     return PBASE;
 }
 
+// r_top >= 0: the unit lower triangle's BASE x BASE diagonal blocks from row
+// r_top on are already converted, block q in slot q
 template <int N>
-void trsm_rec(Ctx& c, long long r, int b, long long j0, int ncols, bool lower) {
+void trsm_rec(Ctx& c, long long r, int b, long long j0, int ncols, bool lower, long long r_top = -1) {
     if (c.rc || ncols <= 0) return;
+    // (a power of two: the halving recursion then ends on the BASE blocks)
+    if (lower && r_top < 0 && b > BASE && (b & (b - 1)) == 0 && b / BASE <= TRI_SLOTS) {
+        // every leaf's triangle in one launch, ahead of the recursion
+        c.h->phase(PH_TRSM);
+        tri_convert_kernel<N><<<dim3((BASE * BASE + 255) / 256, b / BASE), 256, 0, c.h->stream>>>(
+            at(c, r, r), c.lda, BASE, 1, c.sc);
+        c.h->count(1);
+        r_top = r;
+    }
     if (b <= BASE) {
         c.h->phase(PH_TRSM);
-        trsm_base<N>(at(c, r, r), c.lda, at(c, r, j0), c.lda, b, ncols, lower ? 1 : 0, c.sc, c.h->stream);
-        c.h->count(2);
+        const int slot = (lower && r_top >= 0) ? (int)((r - r_top) / BASE) : -1;
+        trsm_base<N>(at(c, r, r), c.lda, at(c, r, j0), c.lda, b, ncols, lower ? 1 : 0, c.sc, c.h->stream, slot);
+        c.h->count(slot < 0 ? 2 : 1);
         return;
     }
     const int b1 = b / 2;
     if (lower) {
-        trsm_rec<N>(c, r, b1, j0, ncols, true);
+        trsm_rec<N>(c, r, b1, j0, ncols, true, r_top);
         c.rc = c.rc ? c.rc : gemm_device(c.h, N, c.p, b - b1, ncols, b1, -1, at(c, r + b1, r), c.lda,
                                          at(c, r, j0), c.lda, 1, at(c, r + b1, j0), c.lda, c.opts);
-        trsm_rec<N>(c, r + b1, b - b1, j0, ncols, true);
+        trsm_rec<N>(c, r + b1, b - b1, j0, ncols, true, r_top);
     } else {
         trsm_rec<N>(c, r + b1, b - b1, j0, ncols, false);
         c.rc = c.rc ? c.rc : gemm_device(c.h, N, c.p, b1, ncols, b - b1, -1, at(c, r, r + b1), c.lda,
